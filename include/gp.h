@@ -1,0 +1,218 @@
+/*
+ * gp.h -- C-ABI of the B300 (sm_103a) multilevel CPU/GPU bipartitioner for weighted task DAGs.
+ *
+ * The operation (Wu, Lohmann, Schroeder-Preikschat, "A Graph-Partition-Based Scheduling Policy for
+ * Heterogeneous Architectures"): a task DAG whose vertices carry a CPU and a GPU kernel time and whose
+ * edges carry a transfer time, the same in both directions (Sec. III.B), is split into a CPU side and a
+ * GPU side (k = 2, Sec. III.B) so that both sides stay within load bounds derived from the workload
+ * ratio of Eq. (1)-(2) and the transfer cost of cut edges is small (Sec. IV.C).  The makespan of the
+ * resulting mapping is then evaluated exactly.  The multilevel algorithm (the paper delegates it to
+ * METIS) is deterministic: results are bit-identical from run to run and to the CPU oracle.
+ *
+ * Conventions
+ *   - vertex ids are int32 (n <= 2^31 - 2); CSR row pointers are int64; times are integer ns.
+ *   - part[v] is uint8: 0 = CPU side, 1 = GPU side.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is stream-ordered and
+ *     returns after the results it reports to the host are available.
+ *   - "device or host" pointers are classified with cudaPointerGetAttributes; pinned, pageable,
+ *     managed and device memory are all accepted there.
+ *   - Calls never throw; failures are reported as gp_status.  A gp_graph handle is not thread-safe;
+ *     distinct handles may be used from distinct threads.
+ *   - All device memory the library allocates comes from the current device's stream-ordered pool.
+ */
+#ifndef GP_H
+#define GP_H
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GP_API __attribute__((visibility("default")))
+#else
+#define GP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gp_status {
+  GP_OK = 0,
+  GP_ERR_INVALID = 1,  /* malformed CSR, id out of range, negative cost, bad argument     */
+  GP_ERR_NOT_DAG = 2,  /* the graph has a cycle (a self-loop counts as one)               */
+  GP_ERR_OOM = 3,      /* a device or host allocation failed                              */
+  GP_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed                     */
+  GP_ERR_TIMEOUT = 5,  /* a device-side wait (grid barrier) exceeded its iteration limit  */
+  GP_ERR_OVERFLOW = 6  /* a summed cost exceeds 2^61 ns                                   */
+} gp_status;
+
+typedef struct gp_graph gp_graph; /* opaque; owns device copies of the DAG */
+
+/* Result of one bipartition. */
+typedef struct gp_result {
+  int64_t cut;        /* sum of transfer costs of directed edges with ends on different sides   */
+  int64_t load_cpu;   /* sum of CPU times of CPU-side vertices                                   */
+  int64_t load_gpu;   /* sum of GPU times of GPU-side vertices                                   */
+  int64_t bound_cpu;  /* B_C                                                                     */
+  int64_t bound_gpu;  /* B_G                                                                     */
+  int32_t feasible;   /* load_cpu <= bound_cpu && load_gpu <= bound_gpu                          */
+  int32_t levels;     /* number of contractions                                                  */
+  int32_t rounds;     /* gain rounds run, summed over levels                                     */
+  int32_t coarsest_n; /* vertices of the coarsest graph                                          */
+  int64_t alg_bytes;  /* algorithmic bytes moved by the kernels of this call (see DESIGN)        */
+  float ms[8];        /* phase times in ms when profiling is on: coarsen, initial, refine, cut   */
+} gp_result;
+
+/* Per-level record of the last gp_partition call on a handle (levels 0..levels). */
+#define GP_MAX_LEVELS 48
+typedef struct gp_trace {
+  int32_t levels;
+  int32_t gggp_trial;                 /* winning growing trial, -1 when all-GPU was feasible */
+  int64_t n[GP_MAX_LEVELS + 1];       /* vertices                                            */
+  int64_t a[GP_MAX_LEVELS + 1];       /* adjacency entries                                   */
+  int32_t rounds[GP_MAX_LEVELS + 1];  /* gain rounds run at the level                        */
+  int64_t moves[GP_MAX_LEVELS + 1];   /* gain-round moves at the level                       */
+  int32_t balanced[GP_MAX_LEVELS + 1];/* 1 if a balance round ran                            */
+  int64_t bal_moves[GP_MAX_LEVELS + 1];
+} gp_trace;
+
+/* ---------------------------------------------------------------------------------------------
+ * gp_graph_create -- copy a DAG to the device, validate it, and build what the path needs:
+ * the transposed CSR, the undirected weighted graph the cut is measured on (every directed entry
+ * u->v of cost w adds w to both W(u,v) and W(v,u): transfer time is direction-free, Sec. III.B),
+ * and the topological levels the makespan walks.
+ *   n, m       vertex and directed-edge counts (n >= 0, m >= 0)
+ *   offsets    int64[n+1] out-CSR row pointers (offsets[0] = 0, offsets[n] = m, non-decreasing)
+ *   cols       int32[m]   successor of each edge, in [0, n); parallel entries are allowed
+ *   edge_cost  int32[m]   transfer time of each edge (>= 0)
+ *   cpu_cost   int32[n]   kernel time on the CPU (>= 0)
+ *   gpu_cost   int32[n]   kernel time on the GPU (>= 0)
+ *   ptr_kind   0: the five arrays are host memory, 1: device memory of the current device
+ *   out        receives the handle; the caller keeps ownership of the inputs (they are copied).
+ * Errors: GP_ERR_INVALID, GP_ERR_OVERFLOW, GP_ERR_NOT_DAG (precedence in that order), GP_ERR_OOM,
+ * GP_ERR_CUDA, GP_ERR_TIMEOUT.  On error *out is NULL.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                          const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                          int ptr_kind, void* stream, gp_graph** out);
+
+GP_API gp_status gp_graph_destroy(gp_graph* g);
+
+/* Sizes of a handle: vertices, edges, undirected adjacency entries, topological levels, and the
+ * summed CPU / GPU kernel times (SC, SG of Eq. (1)). Any pointer may be NULL. */
+GP_API gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* m, int64_t* a0, int32_t* nlevels,
+                        int64_t* sum_cpu, int64_t* sum_gpu);
+
+/* Copy out the undirected level-0 graph (compact CSR, rows sorted by neighbour): off int64[n+1],
+ * adj int32[a0], W int64[a0]; and the topological level of every vertex, level int32[n]
+ * (0 for a vertex without predecessors, else 1 + the largest level of its predecessors).
+ * Destinations may be host or device memory; any may be NULL. */
+GP_API gp_status gp_graph_export(const gp_graph* g, int64_t* off, int32_t* adj, int64_t* W, int32_t* level,
+                          void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * gp_bounds -- balance bounds from Eq. (1)-(2), exact integers.
+ *   r_cpu < 0: Eq. (1) over the summed times: T* = floor(SC*SG/(SC+SG)) (0 when SC+SG = 0), and
+ *              B_C = B_G = floor(T* * (1e6 + round(tol*1e6)) / 1e6).
+ *   r_cpu in [0, 1]: the CPU takes share r (quantised to 32 fraction bits, Eq. (2) gives the GPU
+ *              1 - r): B_C = floor(floor(SC*r) * (1e6+tol_ppm)/1e6), B_G likewise with SG*(1-r).
+ *   tol in [0, 1].  Errors: GP_ERR_INVALID for r_cpu > 1 or NaN, tol outside [0, 1], SC or SG < 0.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_bounds(int64_t sum_cpu, int64_t sum_gpu, double r_cpu, double tol, int64_t* bound_cpu,
+                    int64_t* bound_gpu);
+
+/* ---------------------------------------------------------------------------------------------
+ * gp_partition -- the multilevel bipartition (coarsening by handshake heavy-edge matching with
+ * two-hop pairing, greedy graph growing on the coarsest graph, balance and synchronous gain rounds
+ * while uncoarsening).  Balance targets from gp_bounds(SC, SG, r_cpu, tol).
+ *   part_out  uint8[n], host or device; receives the split
+ *   res       host gp_result, may be NULL
+ *   seed      selects the tie-break hash and the growing trials' start vertices
+ * An infeasible final split still returns GP_OK with res->feasible = 0.
+ * Errors: GP_ERR_INVALID (bad r_cpu/tol, NULL handle or part_out), GP_ERR_OOM, GP_ERR_CUDA.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uint8_t* part_out,
+                       gp_result* res, void* stream);
+
+/* Per-level record of the last gp_partition call on g (host struct). */
+GP_API gp_status gp_last_trace(const gp_graph* g, gp_trace* trace);
+
+/* ---------------------------------------------------------------------------------------------
+ * gp_makespan -- makespan of a mapping with unbounded workers per side:
+ *   finish(v) = t_side(v)(v) + max over entries u->v of (finish(u) + [side(u) != side(v)] * w(u,v)),
+ *   the max over no entries being 0; makespan = max_v finish(v) (0 when n = 0).
+ * Evaluated level by level over the topological levels, in int64.
+ *   part        uint8[n] (0/1), host or device
+ *   makespan    host int64, receives the result
+ *   finish_out  int64[n] host or device, may be NULL; receives finish(v)
+ * Errors: GP_ERR_INVALID (NULL arguments or part[v] > 1), GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan, int64_t* finish_out,
+                      void* stream);
+
+/* Cut of a split: sum of edge costs of directed edges whose ends are on different sides. */
+GP_API gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Step-level entry points.  They run one step of the path on a caller-supplied undirected level
+ * graph held in DEVICE memory, in compact CSR form (off int64[n+1], adj int32[a] sorted within
+ * each row, symmetric, no self entries; W int64[a]; vertex weights vC, vG int64[n]).  The caller
+ * owns all buffers.  They exist so that each step can be checked on its own.
+ * ------------------------------------------------------------------------------------------- */
+
+/* Handshake heavy-edge matching: `rounds` synchronous rounds; each unmatched vertex picks its
+ * eligible unmatched neighbour (merged weights within cap_cpu / cap_gpu) with the largest edge
+ * under (W desc, h(seed, min, max) desc, min asc, max asc); mutual picks match.  If twohop != 0,
+ * the vertices left unmatched are then paired two by two per anchor (best neighbour), walking each
+ * anchor's row in neighbour order and skipping pairs over the caps.  mate_out int32[n]: partner or
+ * -1. */
+GP_API gp_status gp_step_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                        const int64_t* vC, const int64_t* vG, int64_t cap_cpu, int64_t cap_gpu,
+                        uint64_t seed, int32_t rounds, int32_t twohop, int32_t* mate_out, void* stream);
+
+/* Contraction of a matching: representatives (unmatched, or the smaller of a pair) are numbered in
+ * vertex order; cmap_out int32[n]; coarse graph written in compact CSR to coff int64[n+1] (first
+ * nc+1 used), cadj int32[a], cW int64[a], cvC / cvG int64[n] (first nc used); *nc_out, *ac_out
+ * receive the coarse sizes (host). */
+GP_API gp_status gp_step_contract(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                           const int64_t* vC, const int64_t* vG, const int32_t* mate, int32_t* cmap_out,
+                           int64_t* coff, int32_t* cadj, int64_t* cW, int64_t* cvC, int64_t* cvG,
+                           int64_t* nc_out, int64_t* ac_out, void* stream);
+
+/* Greedy graph growing: all-GPU if sum vG <= bound_gpu, else the best of 8 trials; part_out
+ * uint8[n] (device), *trial_out (host) = winning trial or -1. */
+GP_API gp_status gp_step_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                       const int64_t* vC, const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu,
+                       uint64_t seed, uint8_t* part_out, int32_t* trial_out, void* stream);
+
+/* One growing trial from `start` (0 <= start < n): part_out uint8[n] (device), *cut_out (host). */
+GP_API gp_status gp_step_gggp_grow(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                            const int64_t* vC, const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu,
+                            int64_t start, uint8_t* part_out, int64_t* cut_out, void* stream);
+
+/* Refinement at one level: a balance round if the split is infeasible, then up to 8 gain rounds
+ * (round r moves vertices with positive gain from side r mod 2, in (gain desc, id asc) order, the
+ * longest prefix that keeps the destination within its bound), stopping after two consecutive
+ * empty rounds.  part (device, uint8[n]) is updated in place.  stats (host int64[6], may be NULL):
+ * rounds, balanced, moves, balance moves, load_cpu, load_gpu. */
+GP_API gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                         const int64_t* vC, const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu,
+                         uint8_t* part, int64_t* stats, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Instrumentation.
+ * gp_launch_count: kernels launched by this library since load (all threads).
+ * gp_prof_enable(1): record CUDA events around every launch of each kernel family (on the
+ *   launching stream) and accumulate their durations; gp_prof_read returns launches and total ms of
+ *   family `kernel` (see gp_kernel_name) and its algorithmic bytes; gp_prof_reset clears them.
+ * ------------------------------------------------------------------------------------------- */
+GP_API int64_t gp_launch_count(void);
+GP_API gp_status gp_prof_enable(int on);
+GP_API gp_status gp_prof_reset(void);
+GP_API gp_status gp_prof_read(int kernel, int64_t* launches, double* total_ms, int64_t* alg_bytes);
+GP_API const char* gp_kernel_name(int kernel); /* NULL past the last family */
+
+GP_API const char* gp_status_string(gp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

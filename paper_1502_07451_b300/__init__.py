@@ -1,0 +1,339 @@
+"""B300-native multilevel CPU/GPU bipartitioner for weighted task DAGs.
+
+Python binding of the C-ABI in ``include/gp.h``: argument marshalling only.
+Every step of the path runs in the CUDA library ``libgp.so`` (sm_103a),
+built in-tree by ``build.py``; if it cannot be built or loaded, every call
+raises.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays; device
+tensors are passed as device pointers, everything else as host pointers.
+
+The method (Wu, Lohmann, Schroeder-Preikschat, Sec. III.B, Eq. (1)-(2)):
+split a DAG with per-vertex CPU/GPU kernel times and per-edge transfer times
+into a CPU side and a GPU side under load bounds from the workload ratio,
+minimising the transfer cost of cut edges; then evaluate the makespan.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GP_OK, GP_ERR_INVALID, GP_ERR_NOT_DAG, GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_OVERFLOW = range(7)
+MAX_LEVELS = 48
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = "%s failed: %s (status %d)" % (where, status_string(status) if _lib else "?", status)
+        super().__init__(msg)
+        self.status = status
+
+
+class Result(C.Structure):
+    _fields_ = [("cut", C.c_int64), ("load_cpu", C.c_int64), ("load_gpu", C.c_int64),
+                ("bound_cpu", C.c_int64), ("bound_gpu", C.c_int64), ("feasible", C.c_int32),
+                ("levels", C.c_int32), ("rounds", C.c_int32), ("coarsest_n", C.c_int32),
+                ("alg_bytes", C.c_int64), ("ms", C.c_float * 8)]
+
+    def as_dict(self):
+        d = {f[0]: int(getattr(self, f[0])) for f in self._fields_ if f[0] != "ms"}
+        d["ms"] = [float(x) for x in self.ms]
+        return d
+
+
+_L1 = MAX_LEVELS + 1
+
+
+class Trace(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("gggp_trial", C.c_int32), ("n", C.c_int64 * _L1),
+                ("a", C.c_int64 * _L1), ("rounds", C.c_int32 * _L1), ("moves", C.c_int64 * _L1),
+                ("balanced", C.c_int32 * _L1), ("bal_moves", C.c_int64 * _L1)]
+
+    def as_dict(self):
+        L = self.levels
+        return dict(levels=L, gggp_trial=self.gggp_trial, n=list(self.n[:L + 1]), a=list(self.a[:L + 1]),
+                    rounds=list(self.rounds[:L + 1]), moves=list(self.moves[:L + 1]),
+                    balanced=list(self.balanced[:L + 1]), bal_moves=list(self.bal_moves[:L + 1]))
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_I32 = C.c_int32
+_U64 = C.c_uint64
+_D = C.c_double
+
+
+def lib():
+    """The loaded libgp.so (built in-tree on first use if missing or older than its sources)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            sig = {
+                "gp_graph_create": [_I64, _I64, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)],
+                "gp_graph_destroy": [_P],
+                "gp_graph_info": [_P, _P, _P, _P, _P, _P, _P],
+                "gp_graph_export": [_P, _P, _P, _P, _P, _P],
+                "gp_bounds": [_I64, _I64, _D, _D, _P, _P],
+                "gp_partition": [_P, _D, _D, _U64, _P, _P, _P],
+                "gp_last_trace": [_P, _P],
+                "gp_makespan": [_P, _P, _P, _P, _P],
+                "gp_cut": [_P, _P, _P, _P],
+                "gp_step_match": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _I32, _I32, _P, _P],
+                "gp_step_contract": [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+                "gp_step_gggp": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _P, _P, _P],
+                "gp_step_gggp_grow": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _I64, _P, _P, _P],
+                "gp_step_refine": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _P, _P, _P],
+                "gp_prof_enable": [C.c_int],
+                "gp_prof_reset": [],
+                "gp_prof_read": [C.c_int, _P, _P, _P],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = C.c_int
+            L.gp_status_string.argtypes = [C.c_int]
+            L.gp_status_string.restype = C.c_char_p
+            L.gp_kernel_name.argtypes = [C.c_int]
+            L.gp_kernel_name.restype = C.c_char_p
+            L.gp_launch_count.argtypes = []
+            L.gp_launch_count.restype = C.c_int64
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def status_string(st: int) -> str:
+    return lib().gp_status_string(st).decode()
+
+
+def _check(st: int, where: str):
+    if st != GP_OK:
+        raise GpError(st, where)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """(pointer, is_device) of a torch tensor / numpy array / None."""
+    if x is None:
+        return None, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), bool(x.is_cuda)
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, False
+    raise TypeError("expected a torch tensor or a numpy array, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# C-ABI, same names
+# ---------------------------------------------------------------------------
+
+def gp_graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, stream=None):
+    """Copy a DAG (out-CSR + costs) to the device and validate it; returns the handle."""
+    arrs = [offsets, cols, edge_cost, cpu_cost, gpu_cost]
+    ptrs = [_ptr(a) for a in arrs]
+    kinds = {dev for (_, dev) in ptrs}
+    if len(kinds) != 1:
+        raise ValueError("all five arrays must live on the same side (host or device)")
+    h = _P()
+    st = lib().gp_graph_create(int(n), int(m), *[p for p, _ in ptrs], 1 if kinds.pop() else 0, _stream(stream),
+                               C.byref(h))
+    _check(st, "gp_graph_create")
+    return h
+
+
+def gp_graph_destroy(h):
+    _check(lib().gp_graph_destroy(h), "gp_graph_destroy")
+
+
+def gp_graph_info(h):
+    v = [C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64()]
+    _check(lib().gp_graph_info(h, *[C.byref(x) for x in v]), "gp_graph_info")
+    return dict(n=v[0].value, m=v[1].value, a0=v[2].value, nlevels=v[3].value, sum_cpu=v[4].value,
+                sum_gpu=v[5].value)
+
+
+def gp_graph_export(h, off=None, adj=None, W=None, level=None, stream=None):
+    _check(lib().gp_graph_export(h, _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(level)[0], _stream(stream)),
+           "gp_graph_export")
+
+
+def gp_bounds(sum_cpu, sum_gpu, r_cpu=-1.0, tol=0.03):
+    bc, bg = C.c_int64(), C.c_int64()
+    _check(lib().gp_bounds(int(sum_cpu), int(sum_gpu), float(r_cpu), float(tol), C.byref(bc), C.byref(bg)),
+           "gp_bounds")
+    return int(bc.value), int(bg.value)
+
+
+def gp_partition(h, r_cpu, tol, seed, part_out, stream=None):
+    res = Result()
+    _check(lib().gp_partition(h, float(r_cpu), float(tol), int(seed), _ptr(part_out)[0], C.byref(res),
+                              _stream(stream)), "gp_partition")
+    return res.as_dict()
+
+
+def gp_last_trace(h):
+    t = Trace()
+    _check(lib().gp_last_trace(h, C.byref(t)), "gp_last_trace")
+    return t.as_dict()
+
+
+def gp_makespan(h, part, finish_out=None, stream=None):
+    ms = C.c_int64()
+    _check(lib().gp_makespan(h, _ptr(part)[0], C.byref(ms), _ptr(finish_out)[0], _stream(stream)), "gp_makespan")
+    return int(ms.value)
+
+
+def gp_cut(h, part, stream=None):
+    c = C.c_int64()
+    _check(lib().gp_cut(h, _ptr(part)[0], C.byref(c), _stream(stream)), "gp_cut")
+    return int(c.value)
+
+
+def gp_step_match(n, off, adj, W, vC, vG, cap_cpu, cap_gpu, seed, rounds, twohop, mate_out, stream=None):
+    _check(lib().gp_step_match(int(n), _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(vC)[0], _ptr(vG)[0],
+                               int(cap_cpu), int(cap_gpu), int(seed), int(rounds), int(twohop),
+                               _ptr(mate_out)[0], _stream(stream)), "gp_step_match")
+
+
+def gp_step_contract(n, off, adj, W, vC, vG, mate, cmap_out, coff, cadj, cW, cvC, cvG, stream=None):
+    nc, ac = C.c_int64(), C.c_int64()
+    _check(lib().gp_step_contract(int(n), _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(vC)[0], _ptr(vG)[0],
+                                  _ptr(mate)[0], _ptr(cmap_out)[0], _ptr(coff)[0], _ptr(cadj)[0], _ptr(cW)[0],
+                                  _ptr(cvC)[0], _ptr(cvG)[0], C.byref(nc), C.byref(ac), _stream(stream)),
+           "gp_step_contract")
+    return int(nc.value), int(ac.value)
+
+
+def gp_step_gggp(n, off, adj, W, vC, vG, bound_cpu, bound_gpu, seed, part_out, stream=None):
+    t = C.c_int32()
+    _check(lib().gp_step_gggp(int(n), _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(vC)[0], _ptr(vG)[0],
+                              int(bound_cpu), int(bound_gpu), int(seed), _ptr(part_out)[0], C.byref(t),
+                              _stream(stream)), "gp_step_gggp")
+    return int(t.value)
+
+
+def gp_step_gggp_grow(n, off, adj, W, vC, vG, bound_cpu, bound_gpu, start, part_out, stream=None):
+    c = C.c_int64()
+    _check(lib().gp_step_gggp_grow(int(n), _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(vC)[0], _ptr(vG)[0],
+                                   int(bound_cpu), int(bound_gpu), int(start), _ptr(part_out)[0], C.byref(c),
+                                   _stream(stream)), "gp_step_gggp_grow")
+    return int(c.value)
+
+
+def gp_step_refine(n, off, adj, W, vC, vG, bound_cpu, bound_gpu, part, stream=None):
+    st = (C.c_int64 * 6)()
+    _check(lib().gp_step_refine(int(n), _ptr(off)[0], _ptr(adj)[0], _ptr(W)[0], _ptr(vC)[0], _ptr(vG)[0],
+                                int(bound_cpu), int(bound_gpu), _ptr(part)[0], st, _stream(stream)),
+           "gp_step_refine")
+    return dict(rounds=st[0], balanced=st[1], moves=st[2], bal_moves=st[3], load_cpu=st[4], load_gpu=st[5])
+
+
+def gp_launch_count() -> int:
+    return int(lib().gp_launch_count())
+
+
+def gp_prof_enable(on: bool):
+    _check(lib().gp_prof_enable(1 if on else 0), "gp_prof_enable")
+
+
+def gp_prof_reset():
+    _check(lib().gp_prof_reset(), "gp_prof_reset")
+
+
+def gp_prof_read(kernel: int):
+    n, ms, b = C.c_int64(), C.c_double(), C.c_int64()
+    _check(lib().gp_prof_read(int(kernel), C.byref(n), C.byref(ms), C.byref(b)), "gp_prof_read")
+    return dict(launches=int(n.value), total_ms=float(ms.value), alg_bytes=int(b.value))
+
+
+def gp_kernel_name(kernel: int):
+    r = lib().gp_kernel_name(int(kernel))
+    return r.decode() if r is not None else None
+
+
+def kernel_families():
+    out = []
+    k = 0
+    while True:
+        name = gp_kernel_name(k)
+        if name is None:
+            return out
+        out.append(name)
+        k += 1
+
+
+# ---------------------------------------------------------------------------
+# Convenience: a handle that owns its device graph
+# ---------------------------------------------------------------------------
+
+class Graph:
+    """Device copy of a DAG given as a dict of arrays (see gen.py), torch or numpy."""
+
+    def __init__(self, g, stream=None):
+        self.n, self.m = int(g["n"]), int(g["m"])
+        self.h = gp_graph_create(self.n, self.m, g["offsets"], g["cols"], g["edge_cost"], g["cpu_cost"],
+                                 g["gpu_cost"], stream=stream)
+
+    def info(self):
+        return gp_graph_info(self.h)
+
+    def partition(self, part_out, r_cpu=-1.0, tol=0.03, seed=0, stream=None):
+        return gp_partition(self.h, r_cpu, tol, seed, part_out, stream)
+
+    def makespan(self, part, finish_out=None, stream=None):
+        return gp_makespan(self.h, part, finish_out, stream)
+
+    def cut(self, part, stream=None):
+        return gp_cut(self.h, part, stream)
+
+    def trace(self):
+        return gp_last_trace(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            gp_graph_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,935 @@
+// gp_api.cu -- the C-ABI (include/gp.h) of the B300 multilevel CPU/GPU bipartitioner.
+// Single translation unit: the kernel headers are included here.
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "gp_internal.cuh"
+#include "k_scan.cuh"
+#include "k_rows.cuh"
+#include "k_graph.cuh"
+#include "k_coarsen.cuh"
+#include "k_initial.cuh"
+#include "k_refine.cuh"
+#include "k_makespan.cuh"
+
+namespace gp {
+
+const char* const kFamilyName[F_COUNT] = {
+    "validate", "transpose", "levels", "sym_merge", "match_pick", "match_confirm", "twohop", "cmap",
+    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc"};
+
+// ------------------------------------------------------------------------------------------------
+// launch accounting and optional per-launch event timing
+// ------------------------------------------------------------------------------------------------
+static std::atomic<long long> g_launches{0};
+static std::atomic<int> g_prof{0};
+struct EvRec {
+  int fam;
+  cudaEvent_t a, b;
+};
+static std::mutex g_ev_mu;
+static std::vector<EvRec> g_ev;
+static std::vector<cudaEvent_t> g_ev_pool;
+static thread_local cudaEvent_t t_pending = nullptr;
+static double g_fam_ms[F_COUNT];
+static long long g_fam_launches[F_COUNT];
+
+static cudaEvent_t ev_get() {
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  if (!g_ev_pool.empty()) {
+    cudaEvent_t e = g_ev_pool.back();
+    g_ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+bool prof_on() { return g_prof.load() != 0; }
+
+void launch_begin(int family, cudaStream_t s) {
+  g_launches.fetch_add(1);
+  if (prof_on()) {
+    t_pending = ev_get();
+    if (t_pending) cudaEventRecord(t_pending, s);
+  }
+  (void)family;
+}
+
+void launch_end(int family, cudaStream_t s) {
+  if (prof_on() && t_pending) {
+    cudaEvent_t b = ev_get();
+    if (b) {
+      cudaEventRecord(b, s);
+      std::lock_guard<std::mutex> lk(g_ev_mu);
+      g_ev.push_back(EvRec{family, t_pending, b});
+    }
+    t_pending = nullptr;
+  }
+}
+
+static void prof_collect() {
+  std::lock_guard<std::mutex> lk(g_ev_mu);
+  for (auto& r : g_ev) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      g_fam_ms[r.fam] += ms;
+      g_fam_launches[r.fam] += 1;
+    }
+    g_ev_pool.push_back(r.a);
+    g_ev_pool.push_back(r.b);
+  }
+  g_ev.clear();
+}
+
+cudaError_t launch_coop(int family, const void* fn, int grid, int block, size_t smem, cudaStream_t s,
+                        void** args) {
+  launch_begin(family, s);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
+  launch_end(family, s);
+  return e;
+}
+
+// ------------------------------------------------------------------------------------------------
+// device memory: the current device's stream-ordered pool, kept cached across calls
+// ------------------------------------------------------------------------------------------------
+static std::mutex g_dev_mu;
+static bool g_pool_set[64];
+static int g_sms[64];
+
+int device_id() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
+int num_sms() {
+  const int d = device_id();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (d >= 0 && d < 64 && g_sms[d] == 0) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d);
+    g_sms[d] = v > 0 ? v : 1;
+  }
+  return (d >= 0 && d < 64) ? g_sms[d] : 1;
+}
+
+static void pool_setup() {
+  const int d = device_id();
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (d < 0 || d >= 64 || g_pool_set[d]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, d) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  g_pool_set[d] = true;
+}
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  const char* f = getenv("GP_FAULT");
+  if (f && strcmp(f, "oom") == 0) throw Fail{GP_ERR_OOM};
+  GP_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, s));
+  return p;
+}
+
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+// per-call allocations released at scope exit (stream-ordered)
+struct Arena {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Arena(cudaStream_t st) : s(st) {}
+  template <class T>
+  T* get(int64_t count) {
+    T* p = dnew<T>(count, s);
+    ptrs.push_back(p);
+    return p;
+  }
+  ~Arena() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+static int coop_blocks_per_sm(const void* fn, int block, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, smem) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static gp_status host_bounds(int64_t SC, int64_t SG, double r_cpu, double tol, int64_t* BC, int64_t* BG) {
+  if (!(tol >= 0.0 && tol <= 1.0)) return GP_ERR_INVALID;
+  if (std::isnan(r_cpu) || r_cpu > 1.0) return GP_ERR_INVALID;
+  if (SC < 0 || SG < 0) return GP_ERR_INVALID;
+  const __int128 ppm = (__int128)llround(tol * 1e6);
+  const __int128 scale = (__int128)1000000 + ppm;
+  if (r_cpu < 0.0) {
+    const __int128 den = (__int128)SC + (__int128)SG;
+    const __int128 t = den == 0 ? 0 : ((__int128)SC * (__int128)SG) / den;
+    *BC = (int64_t)((t * scale) / 1000000);
+    *BG = *BC;
+  } else {
+    const __int128 rq = (__int128)llround(r_cpu * 4294967296.0);
+    const __int128 tc = ((__int128)SC * rq) >> 32;
+    const __int128 tg = ((__int128)SG * (((__int128)1 << 32) - rq)) >> 32;
+    *BC = (int64_t)((tc * scale) / 1000000);
+    *BG = (int64_t)((tg * scale) / 1000000);
+  }
+  return GP_OK;
+}
+
+static int makespan_group(int64_t n, int64_t m) {
+  const double avg = n > 0 ? (double)m / (double)n : 0.0;
+  if (avg <= 3.0) return 2;
+  if (avg <= 6.0) return 4;
+  if (avg <= 12.0) return 8;
+  if (avg <= 24.0) return 16;
+  return 32;
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+struct gp_graph {
+  int dev = 0;
+  int64_t n = 0, m = 0, a0 = 0;
+  int32_t nlev = 0;
+  int64_t SC = 0, SG = 0;
+  int64_t max_width = 0;
+  int64_t* off = nullptr;
+  int32_t* cols = nullptr;
+  int32_t* w = nullptr;
+  int32_t* cC = nullptr;
+  int32_t* cG = nullptr;
+  int64_t* lev_ptr = nullptr;
+  int32_t* lev_vtx = nullptr;
+  int32_t* level = nullptr;
+  int64_t* lo_off = nullptr;
+  int32_t* lo_src = nullptr;
+  int32_t* lo_w = nullptr;
+  int32_t* lo_cC = nullptr;
+  int32_t* lo_cG = nullptr;
+  LevelGraph L0;
+  gp_trace trace;
+  std::vector<void*> owned;
+  template <class T>
+  T* own(int64_t count, cudaStream_t s) {
+    T* p = dnew<T>(count, s);
+    owned.push_back(p);
+    return p;
+  }
+};
+
+static void graph_free(gp_graph* g) {
+  if (!g) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(g->dev);
+  cudaDeviceSynchronize();
+  for (void* p : g->owned) cudaFree(p);
+  cudaSetDevice(cur);
+  delete g;
+}
+
+extern "C" {
+
+const char* gp_status_string(gp_status s) {
+  switch (s) {
+    case GP_OK: return "ok";
+    case GP_ERR_INVALID: return "invalid argument or malformed graph";
+    case GP_ERR_NOT_DAG: return "graph has a cycle";
+    case GP_ERR_OOM: return "out of memory";
+    case GP_ERR_CUDA: return "CUDA error";
+    case GP_ERR_TIMEOUT: return "device wait timed out";
+    case GP_ERR_OVERFLOW: return "summed cost exceeds 2^61";
+  }
+  return "unknown status";
+}
+
+int64_t gp_launch_count(void) { return (int64_t)g_launches.load(); }
+
+gp_status gp_prof_enable(int on) {
+  g_prof.store(on ? 1 : 0);
+  return GP_OK;
+}
+
+gp_status gp_prof_reset(void) {
+  prof_collect();
+  for (int i = 0; i < F_COUNT; i++) {
+    g_fam_ms[i] = 0;
+    g_fam_launches[i] = 0;
+  }
+  unsigned long long z[F_COUNT] = {0};
+  if (cudaMemcpyToSymbol(d_alg_bytes, z, sizeof(z)) != cudaSuccess) return GP_ERR_CUDA;
+  return GP_OK;
+}
+
+gp_status gp_prof_read(int kernel, int64_t* launches, double* total_ms, int64_t* alg_bytes) {
+  if (kernel < 0 || kernel >= F_COUNT) return GP_ERR_INVALID;
+  prof_collect();
+  unsigned long long b[F_COUNT];
+  if (cudaMemcpyFromSymbol(b, d_alg_bytes, sizeof(b)) != cudaSuccess) return GP_ERR_CUDA;
+  if (launches) *launches = g_fam_launches[kernel];
+  if (total_ms) *total_ms = g_fam_ms[kernel];
+  if (alg_bytes) *alg_bytes = (int64_t)b[kernel];
+  return GP_OK;
+}
+
+const char* gp_kernel_name(int kernel) {
+  if (kernel < 0 || kernel >= F_COUNT) return nullptr;
+  return kFamilyName[kernel];
+}
+
+gp_status gp_bounds(int64_t sum_cpu, int64_t sum_gpu, double r_cpu, double tol, int64_t* bound_cpu,
+                    int64_t* bound_gpu) {
+  if (!bound_cpu || !bound_gpu) return GP_ERR_INVALID;
+  return host_bounds(sum_cpu, sum_gpu, r_cpu, tol, bound_cpu, bound_gpu);
+}
+
+gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                          const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                          int ptr_kind, void* stream, gp_graph** out) {
+  if (!out) return GP_ERR_INVALID;
+  *out = nullptr;
+  if (n < 0 || m < 0 || n > kMaxN || (ptr_kind != 0 && ptr_kind != 1)) return GP_ERR_INVALID;
+  if (!offsets || (m > 0 && (!cols || !edge_cost)) || (n > 0 && (!cpu_cost || !gpu_cost))) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  gp_graph* g = new gp_graph();
+  try {
+    pool_setup();
+    g->dev = device_id();
+    g->n = n;
+    g->m = m;
+    memset(&g->trace, 0, sizeof(g->trace));
+    g->off = g->own<int64_t>(n + 1, s);
+    g->cols = g->own<int32_t>(m, s);
+    g->w = g->own<int32_t>(m, s);
+    g->cC = g->own<int32_t>(n, s);
+    g->cG = g->own<int32_t>(n, s);
+    const cudaMemcpyKind kind = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    GP_CUDA(cudaMemcpyAsync(g->off, offsets, sizeof(int64_t) * (n + 1), kind, s));
+    if (m) {
+      GP_CUDA(cudaMemcpyAsync(g->cols, cols, sizeof(int32_t) * m, kind, s));
+      GP_CUDA(cudaMemcpyAsync(g->w, edge_cost, sizeof(int32_t) * m, kind, s));
+    }
+    if (n) {
+      GP_CUDA(cudaMemcpyAsync(g->cC, cpu_cost, sizeof(int32_t) * n, kind, s));
+      GP_CUDA(cudaMemcpyAsync(g->cG, gpu_cost, sizeof(int32_t) * n, kind, s));
+    }
+    Arena A(s);
+    // ---- validation (sizes, ids, costs) and exact sums
+    int* flags = A.get<int>(1);
+    unsigned long long* sums = A.get<unsigned long long>(6);
+    GP_CUDA(cudaMemsetAsync(flags, 0, sizeof(int), s));
+    GP_CUDA(cudaMemsetAsync(sums, 0, 6 * sizeof(unsigned long long), s));
+    const int64_t vwork = n > m ? n : m;
+    GP_LAUNCH(F_VALIDATE, k_validate, grid_for(vwork + 1, 256, 8), 256, 0, s, n, m, g->off, g->cols, g->w, g->cC,
+              g->cG, flags, sums);
+    GP_CHECK_LAUNCH();
+    int hflags = 0;
+    unsigned long long hs[6];
+    GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (hflags & VF_INVALID) throw Fail{GP_ERR_INVALID};
+    const unsigned __int128 sw = ((unsigned __int128)hs[1] << 64) | hs[0];
+    const unsigned __int128 sc = ((unsigned __int128)hs[3] << 64) | hs[2];
+    const unsigned __int128 sg = ((unsigned __int128)hs[5] << 64) | hs[4];
+    if (sw > (unsigned __int128)kSumLimit || sc > (unsigned __int128)kSumLimit || sg > (unsigned __int128)kSumLimit)
+      throw Fail{GP_ERR_OVERFLOW};
+    g->SC = (int64_t)sc;
+    g->SG = (int64_t)sg;
+    // ---- transpose (in-CSR) and self-loop check
+    int32_t* indeg = A.get<int32_t>(n);
+    int64_t* in_off = A.get<int64_t>(n + 1);
+    int32_t* in_src = A.get<int32_t>(m);
+    int32_t* in_w = A.get<int32_t>(m);
+    GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
+    if (m) GP_LAUNCH(F_TRANSPOSE, k_indeg, grid_for(m, 256, 8), 256, 0, s, m, g->cols, indeg);
+    scan_i32_to_i64(indeg, in_off, n, s);
+    GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));  // reused as fill cursor
+    if (n) GP_LAUNCH(F_TRANSPOSE, k_fill_in, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off,
+                     indeg, in_src, in_w, flags);
+    GP_CHECK_LAUNCH();
+    // ---- topological levels (cooperative, grid barrier per level)
+    g->lev_vtx = g->own<int32_t>(n, s);
+    g->lev_ptr = g->own<int64_t>(n + 2, s);
+    g->level = g->own<int32_t>(n, s);
+    int32_t* rem = A.get<int32_t>(n);
+    unsigned long long* tail = A.get<unsigned long long>(2);
+    int32_t* nlev_dev = A.get<int32_t>(1);
+    unsigned* bar = A.get<unsigned>(2);
+    int* err = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(tail, 0, 2 * sizeof(unsigned long long), s));
+    GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), s));
+    GP_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+    GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (n) {
+      const int bps = coop_blocks_per_sm((const void*)k_levels, 256, 0);
+      int grid = num_sms() * (bps < 2 ? bps : 2);
+      const int64_t need = (n + 255) / 256;
+      if (need < grid) grid = (int)need;
+      int64_t nn = n;
+      int64_t* off_p = g->off;
+      int32_t* cols_p = g->cols;
+      void* args[] = {&nn, &off_p, &cols_p, &in_off, &rem, &g->lev_vtx, &g->lev_ptr, &g->level, &tail, &nlev_dev, &bar, &err};
+      GP_CUDA(launch_coop(F_LEVELS, (const void*)k_levels, grid, 256, 0, s, args));
+    }
+    unsigned long long htail = 0;
+    int herr = 0;
+    int32_t hnlev = 0;
+    GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&htail, tail, sizeof(htail), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&hnlev, nlev_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (herr) throw Fail{(gp_status)herr};
+    if ((hflags & VF_SELFLOOP) || (int64_t)htail != n) throw Fail{GP_ERR_NOT_DAG};
+    g->nlev = hnlev;
+    {
+      std::vector<int64_t> lp((size_t)hnlev + 1);
+      if (n) GP_CUDA(cudaMemcpy(lp.data(), g->lev_ptr, sizeof(int64_t) * (hnlev + 1), cudaMemcpyDeviceToHost));
+      int64_t mw = 0;
+      for (int l = 0; l < hnlev; l++) mw = std::max(mw, lp[l + 1] - lp[l]);
+      g->max_width = mw;
+    }
+    // ---- level-ordered in-CSR for the makespan
+    int32_t* pos_of = A.get<int32_t>(n);
+    int32_t* lo_deg = A.get<int32_t>(n);
+    g->lo_off = g->own<int64_t>(n + 1, s);
+    g->lo_src = g->own<int32_t>(m, s);
+    g->lo_w = g->own<int32_t>(m, s);
+    g->lo_cC = g->own<int32_t>(n, s);
+    g->lo_cG = g->own<int32_t>(n, s);
+    if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_prep, grid_for(n, 256), 256, 0, s, n, g->lev_vtx, in_off, g->cC, g->cG, pos_of,
+                     lo_deg, g->lo_cC, g->lo_cG);
+    scan_i32_to_i64(lo_deg, g->lo_off, n, s);
+    if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_fill, grid_for(n * 32, 256), 256, 0, s, n, g->lev_vtx, in_off, in_src, in_w,
+                     pos_of, g->lo_off, g->lo_src, g->lo_w);
+    // ---- symmetrisation: row v = out-row(v) + in-row(v), merged (Sec. III.B: one cost per transfer)
+    LevelGraph& L = g->L0;
+    L.n = n;
+    L.cap = 2 * m;
+    L.start = g->own<int64_t>(n + 1, s);
+    L.deg = g->own<int32_t>(n, s);
+    L.adj = g->own<int32_t>(2 * m, s);
+    L.W = g->own<int64_t>(2 * m, s);
+    L.vC = g->own<int64_t>(n, s);
+    L.vG = g->own<int64_t>(n, s);
+    int64_t* rawlen = A.get<int64_t>(n);
+    if (n) {
+      GP_LAUNCH(F_SYM_MERGE, k_rawlen_sym, grid_for(n, 256), 256, 0, s, n, g->off, in_off, rawlen);
+      GP_LAUNCH(F_MISC, k_widen, grid_for(n, 256), 256, 0, s, n, g->cC, g->cG, L.vC, L.vG);
+    }
+    scan_i64(rawlen, L.start, n, s);
+    TwoSrc src{};
+    src.a_start = g->off;
+    src.a_col = g->cols;
+    src.a_w32 = g->w;
+    src.b_start = in_off;
+    src.b_col = in_src;
+    src.b_w32 = in_w;
+    src.drop_self = 0;
+    merge_rows(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s);
+    unsigned long long* a0 = A.get<unsigned long long>(1);
+    GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
+    if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, s, n, L.deg, a0);
+    GP_CHECK_LAUNCH();
+    unsigned long long ha0 = 0;
+    GP_CUDA(cudaMemcpyAsync(&ha0, a0, sizeof(ha0), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    g->a0 = (int64_t)ha0;
+    *out = g;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    graph_free(g);
+    return f.st;
+  }
+}
+
+gp_status gp_graph_destroy(gp_graph* g) {
+  if (!g) return GP_ERR_INVALID;
+  graph_free(g);
+  return GP_OK;
+}
+
+gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* m, int64_t* a0, int32_t* nlevels, int64_t* sum_cpu,
+                        int64_t* sum_gpu) {
+  if (!g) return GP_ERR_INVALID;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (a0) *a0 = g->a0;
+  if (nlevels) *nlevels = g->nlev;
+  if (sum_cpu) *sum_cpu = g->SC;
+  if (sum_gpu) *sum_gpu = g->SG;
+  return GP_OK;
+}
+
+gp_status gp_graph_export(const gp_graph* g, int64_t* off, int32_t* adj, int64_t* W, int32_t* level, void* stream) {
+  if (!g) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    Arena A(s);
+    const int64_t n = g->n;
+    int64_t* coff = A.get<int64_t>(n + 1);
+    int32_t* cadj = A.get<int32_t>(g->a0);
+    int64_t* cW = A.get<int64_t>(g->a0);
+    scan_i32_to_i64(g->L0.deg, coff, n, s);
+    if (n) GP_LAUNCH(F_MISC, k_compact_rows, grid_for(n * 32, 256), 256, 0, s, n, g->L0.start, g->L0.deg, g->L0.adj,
+                     g->L0.W, coff, cadj, cW);
+    GP_CHECK_LAUNCH();
+    if (off) GP_CUDA(cudaMemcpyAsync(off, coff, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s));
+    if (adj && g->a0) GP_CUDA(cudaMemcpyAsync(adj, cadj, sizeof(int32_t) * g->a0, cudaMemcpyDefault, s));
+    if (W && g->a0) GP_CUDA(cudaMemcpyAsync(W, cW, sizeof(int64_t) * g->a0, cudaMemcpyDefault, s));
+    if (level && n) GP_CUDA(cudaMemcpyAsync(level, g->level, sizeof(int32_t) * n, cudaMemcpyDefault, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+// device-side per-level record of one partition call
+struct TraceDev {
+  int32_t rounds[kMaxLevels + 1];
+  long long moves[kMaxLevels + 1];
+  int32_t bal[kMaxLevels + 1];
+  long long balmoves[kMaxLevels + 1];
+  unsigned long long cut;
+  unsigned long long a_last;
+  int32_t trial;
+  int32_t bad;
+  Ctl ctl;
+};
+
+gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uint8_t* part_out, gp_result* res,
+                       void* stream) {
+  if (!g || (!part_out && g->n > 0)) return GP_ERR_INVALID;
+  int64_t BC, BG;
+  gp_status st = host_bounds(g->SC, g->SG, r_cpu, tol, &BC, &BG);
+  if (st != GP_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  gp_result R;
+  memset(&R, 0, sizeof(R));
+  R.bound_cpu = BC;
+  R.bound_gpu = BG;
+  gp_trace T;
+  memset(&T, 0, sizeof(T));
+  T.gggp_trial = -1;
+  const int64_t n = g->n;
+  if (n == 0) {
+    R.feasible = 1;
+    g->trace = T;
+    if (res) *res = R;
+    return GP_OK;
+  }
+  try {
+    Arena A(s);
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    const bool prof = prof_on();
+    if (prof)
+      for (auto& e : ev) cudaEventCreate(&e);
+    if (prof) cudaEventRecord(ev[0], s);
+    std::vector<LevelGraph> L;
+    std::vector<int32_t*> cmaps;
+    L.push_back(g->L0);
+    T.n[0] = n;
+    T.a[0] = g->a0;
+    const int64_t capC = BC / kCapDiv, capG = BG / kCapDiv;
+    TraceDev* td = A.get<TraceDev>(1);
+    GP_CUDA(cudaMemsetAsync(td, 0, sizeof(TraceDev), s));
+    unsigned long long* adev = A.get<unsigned long long>(1);
+    int lev = 0;
+    while (L[lev].n > kCoarsest && lev < kMaxLevels) {
+      const LevelGraph& f = L[lev];
+      int32_t* mate = dnew<int32_t>(f.n, s);
+      int32_t* cmap = A.get<int32_t>(f.n + 1);
+      match_level(f, capC, capG, seed, kMatchRounds, true, mate, s);
+      coarse_count(f, mate, cmap, nullptr, s);
+      int32_t nc = 0;
+      GP_CUDA(cudaMemcpyAsync(&nc, cmap + f.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      if ((int64_t)nc * kStallDen > f.n * kStallNum) {
+        dfree(mate, s);
+        break;
+      }
+      LevelGraph c;
+      c.n = nc;
+      c.cap = T.a[lev];  // the coarse rows hold at most the fine entries
+      contract_level(f, mate, cmap, c, s);
+      dfree(mate, s);
+      A.ptrs.push_back(c.start);
+      A.ptrs.push_back(c.deg);
+      A.ptrs.push_back(c.adj);
+      A.ptrs.push_back(c.W);
+      A.ptrs.push_back(c.vC);
+      A.ptrs.push_back(c.vG);
+      GP_CUDA(cudaMemsetAsync(adev, 0, sizeof(unsigned long long), s));
+      GP_LAUNCH(F_MISC, k_sum_deg, grid_for(nc, 256, 8), 256, 0, s, (int64_t)nc, c.deg, adev);
+      unsigned long long ha = 0;
+      GP_CUDA(cudaMemcpyAsync(&ha, adev, sizeof(ha), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      cmaps.push_back(cmap);
+      L.push_back(c);
+      lev++;
+      T.n[lev] = nc;
+      T.a[lev] = (int64_t)ha;
+    }
+    const int Lc = lev;
+    if (prof) cudaEventRecord(ev[1], s);
+    std::vector<uint8_t*> parts(Lc + 1, nullptr);
+    parts[Lc] = A.get<uint8_t>(L[Lc].n);
+    gggp(L[Lc], BC, BG, g->SG, seed, parts[Lc], &td->trial, s);
+    if (prof) cudaEventRecord(ev[2], s);
+    Ctl hctl;
+    memset(&hctl, 0, sizeof(hctl));
+    hctl.BC = BC;
+    hctl.BG = BG;
+    GP_CUDA(cudaMemcpyAsync(&td->ctl, &hctl, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    refine_loads(L[Lc], parts[Lc], &td->ctl, s);
+    Cands cand;
+    cand.id = A.get<int32_t>(n);
+    cand.gain = A.get<long long>(n);
+    cand.cd = A.get<long long>(n);
+    cand.cs = A.get<long long>(n);
+    for (int l = Lc; l >= 0; l--) {
+      if (l < Lc) {
+        parts[l] = A.get<uint8_t>(L[l].n);
+        project(L[l].n, cmaps[l], parts[l + 1], parts[l], s);
+      }
+      refine_level_run(L[l], parts[l], &td->ctl, cand, s);
+      GP_LAUNCH(F_MISC, k_ref_end, 1, 1, 0, s, &td->ctl, l, td->rounds, td->moves, td->bal, td->balmoves);
+    }
+    if (prof) cudaEventRecord(ev[3], s);
+    GP_LAUNCH(F_CUT, k_cut, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, parts[0], &td->cut, &td->bad);
+    GP_CHECK_LAUNCH();
+    GP_CUDA(cudaMemcpyAsync(part_out, parts[0], (size_t)n, cudaMemcpyDefault, s));
+    if (prof) cudaEventRecord(ev[4], s);
+    TraceDev h;
+    GP_CUDA(cudaMemcpyAsync(&h, td, sizeof(TraceDev), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    R.cut = (int64_t)h.cut;
+    R.load_cpu = h.ctl.LC;
+    R.load_gpu = h.ctl.LG;
+    R.feasible = (h.ctl.LC <= BC && h.ctl.LG <= BG) ? 1 : 0;
+    R.levels = Lc;
+    R.coarsest_n = (int32_t)L[Lc].n;
+    int32_t rounds = 0;
+    for (int l = 0; l <= Lc; l++) {
+      T.rounds[l] = h.rounds[l];
+      T.moves[l] = h.moves[l];
+      T.balanced[l] = h.bal[l];
+      T.bal_moves[l] = h.balmoves[l];
+      rounds += h.rounds[l];
+    }
+    R.rounds = rounds;
+    T.levels = Lc;
+    T.gggp_trial = h.trial;
+    if (prof) {
+      for (int i = 0; i < 4; i++) cudaEventElapsedTime(&R.ms[i], ev[i], ev[i + 1]);
+      for (auto& e : ev) cudaEventDestroy(e);
+    }
+    g->trace = T;
+    if (res) *res = R;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_last_trace(const gp_graph* g, gp_trace* trace) {
+  if (!g || !trace) return GP_ERR_INVALID;
+  *trace = g->trace;
+  return GP_OK;
+}
+
+gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* stream) {
+  if (!g || !cut || (!part && g->n > 0)) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    Arena A(s);
+    const int64_t n = g->n;
+    const uint8_t* p = part;
+    if (n && !is_device_ptr(part)) {
+      uint8_t* d = A.get<uint8_t>(n);
+      GP_CUDA(cudaMemcpyAsync(d, part, (size_t)n, cudaMemcpyDefault, s));
+      p = d;
+    }
+    unsigned long long* c = A.get<unsigned long long>(1);
+    int* bad = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
+    GP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+    if (n) GP_LAUNCH(F_CUT, k_cut, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, p, c, bad);
+    GP_CHECK_LAUNCH();
+    unsigned long long hc = 0;
+    int hb = 0;
+    GP_CUDA(cudaMemcpyAsync(&hc, c, sizeof(hc), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (hb) return GP_ERR_INVALID;
+    *cut = (int64_t)hc;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan, int64_t* finish_out, void* stream) {
+  if (!g || !makespan || (!part && g->n > 0)) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = g->n;
+  if (n == 0) {
+    *makespan = 0;
+    return GP_OK;
+  }
+  try {
+    Arena A(s);
+    const uint8_t* p = part;
+    if (!is_device_ptr(part)) {
+      uint8_t* d = A.get<uint8_t>(n);
+      GP_CUDA(cudaMemcpyAsync(d, part, (size_t)n, cudaMemcpyDefault, s));
+      p = d;
+    }
+    int64_t* fin = nullptr;
+    const bool fin_host = finish_out && !is_device_ptr(finish_out);
+    if (finish_out) fin = fin_host ? A.get<int64_t>(n) : finish_out;
+    unsigned long long* fp = A.get<unsigned long long>(n);
+    struct Small {
+      unsigned long long ms;
+      int bad;
+      int err;
+      unsigned bar[2];
+    };
+    Small* sm = A.get<Small>(1);
+    GP_CUDA(cudaMemsetAsync(sm, 0, sizeof(Small), s));
+    const int G = makespan_group(n, g->m);
+    const void* fn = G == 2 ? (const void*)k_makespan<2>
+                     : G == 4 ? (const void*)k_makespan<4>
+                     : G == 8 ? (const void*)k_makespan<8>
+                     : G == 16 ? (const void*)k_makespan<16> : (const void*)k_makespan<32>;
+    const int bps = coop_blocks_per_sm(fn, 256, 0);
+    const int64_t cap = (int64_t)num_sms() * bps;
+    int64_t want = (g->max_width * G + 255) / 256;
+    if (want < 1) want = 1;
+    const int grid = (int)(want < cap ? want : cap);
+    int32_t nlev = g->nlev;
+    unsigned long long* msp = &sm->ms;
+    int* badp = &sm->bad;
+    int* errp = &sm->err;
+    unsigned* barp = sm->bar;
+    void* args[] = {&nlev, (void*)&g->lev_ptr, (void*)&g->lev_vtx, (void*)&g->lo_off, (void*)&g->lo_src,
+                    (void*)&g->lo_w, (void*)&g->lo_cC, (void*)&g->lo_cG, (void*)&p, &fp, &msp, &badp, &fin,
+                    &barp, &errp};
+    GP_CUDA(launch_coop(F_MAKESPAN, fn, grid, 256, 0, s, args));
+    Small h;
+    GP_CUDA(cudaMemcpyAsync(&h, sm, sizeof(Small), cudaMemcpyDeviceToHost, s));
+    if (fin_host) GP_CUDA(cudaMemcpyAsync(finish_out, fin, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (h.err) return (gp_status)h.err;
+    if (h.bad) return GP_ERR_INVALID;
+    *makespan = (int64_t)h.ms;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// step-level entry points (device CSR in, device results out)
+// ------------------------------------------------------------------------------------------------
+static LevelGraph view_of(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                          const int64_t* vG, Arena& A, cudaStream_t s) {
+  LevelGraph L;
+  L.n = n;
+  L.start = const_cast<int64_t*>(off);
+  L.deg = A.get<int32_t>(n);
+  L.adj = const_cast<int32_t*>(adj);
+  L.W = const_cast<int64_t*>(W);
+  L.vC = const_cast<int64_t*>(vC);
+  L.vG = const_cast<int64_t*>(vG);
+  if (n) GP_LAUNCH(F_MISC, k_deg_from_off, grid_for(n, 256), 256, 0, s, n, off, L.deg);
+  GP_CHECK_LAUNCH();
+  return L;
+}
+
+gp_status gp_step_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                        const int64_t* vG, int64_t cap_cpu, int64_t cap_gpu, uint64_t seed, int32_t rounds,
+                        int32_t twohop, int32_t* mate_out, void* stream) {
+  if (n < 0 || n > kMaxN || !off || (n > 0 && (!vC || !vG || !mate_out)) || rounds < 0) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    LevelGraph L = view_of(n, off, adj, W, vC, vG, A, s);
+    match_level(L, cap_cpu, cap_gpu, seed, rounds, twohop != 0, mate_out, s);
+    GP_CUDA(cudaStreamSynchronize(s));
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_step_contract(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                           const int64_t* vG, const int32_t* mate, int32_t* cmap_out, int64_t* coff, int32_t* cadj,
+                           int64_t* cW, int64_t* cvC, int64_t* cvG, int64_t* nc_out, int64_t* ac_out, void* stream) {
+  if (n < 0 || n > kMaxN || !off || !nc_out || !ac_out || !coff) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    LevelGraph L = view_of(n, off, adj, W, vC, vG, A, s);
+    int64_t a = 0;
+    GP_CUDA(cudaMemcpyAsync(&a, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    int32_t* cmap = A.get<int32_t>(n + 1);
+    coarse_count(L, mate, cmap, nullptr, s);
+    int32_t nc = 0;
+    GP_CUDA(cudaMemcpyAsync(&nc, cmap + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    LevelGraph C;
+    C.n = nc;
+    C.cap = a;
+    if (n) contract_level(L, mate, cmap, C, s);
+    if (n) {
+      A.ptrs.push_back(C.start);
+      A.ptrs.push_back(C.deg);
+      A.ptrs.push_back(C.adj);
+      A.ptrs.push_back(C.W);
+      A.ptrs.push_back(C.vC);
+      A.ptrs.push_back(C.vG);
+      GP_CUDA(cudaMemcpyAsync(cmap_out, cmap, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    scan_i32_to_i64(C.deg, coff, nc, s);
+    if (nc) GP_LAUNCH(F_MISC, k_compact_rows, grid_for((int64_t)nc * 32, 256), 256, 0, s, (int64_t)nc, C.start, C.deg,
+                      C.adj, C.W, coff, cadj, cW);
+    if (nc) {
+      GP_CUDA(cudaMemcpyAsync(cvC, C.vC, sizeof(int64_t) * nc, cudaMemcpyDeviceToDevice, s));
+      GP_CUDA(cudaMemcpyAsync(cvG, C.vG, sizeof(int64_t) * nc, cudaMemcpyDeviceToDevice, s));
+    }
+    GP_CHECK_LAUNCH();
+    int64_t ac = 0;
+    GP_CUDA(cudaMemcpyAsync(&ac, coff + nc, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    *nc_out = nc;
+    *ac_out = ac;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_step_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                       const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu, uint64_t seed, uint8_t* part_out,
+                       int32_t* trial_out, void* stream) {
+  if (n < 0 || n > kMaxN || !off || !trial_out || (n > 0 && !part_out)) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    LevelGraph L = view_of(n, off, adj, W, vC, vG, A, s);
+    long long* sg = A.get<long long>(1);
+    sum_i64(vG, n, sg, s);
+    long long SG = 0;
+    GP_CUDA(cudaMemcpyAsync(&SG, sg, sizeof(SG), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    int32_t* t = A.get<int32_t>(1);
+    GP_CUDA(cudaMemsetAsync(t, 0xff, sizeof(int32_t), s));
+    if (n) gggp(L, bound_cpu, bound_gpu, SG, seed, part_out, t, s);
+    GP_CUDA(cudaMemcpyAsync(trial_out, t, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_step_gggp_grow(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                            const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu, int64_t start, uint8_t* part_out,
+                            int64_t* cut_out, void* stream) {
+  if (n <= 0 || n > kMaxN || !off || start < 0 || start >= n || !part_out || !cut_out) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    LevelGraph L = view_of(n, off, adj, W, vC, vG, A, s);
+    int64_t* c = A.get<int64_t>(1);
+    gggp_grow_one(L, bound_cpu, bound_gpu, start, part_out, c, s);
+    GP_CUDA(cudaMemcpyAsync(cut_out, c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+                         const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu, uint8_t* part, int64_t* stats,
+                         void* stream) {
+  if (n < 0 || n > kMaxN || !off || (n > 0 && !part)) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    LevelGraph L = view_of(n, off, adj, W, vC, vG, A, s);
+    Ctl* ctl = A.get<Ctl>(1);
+    Ctl hc;
+    memset(&hc, 0, sizeof(hc));
+    hc.BC = bound_cpu;
+    hc.BG = bound_gpu;
+    GP_CUDA(cudaMemcpyAsync(ctl, &hc, sizeof(Ctl), cudaMemcpyHostToDevice, s));
+    Cands cand;
+    cand.id = A.get<int32_t>(n);
+    cand.gain = A.get<long long>(n);
+    cand.cd = A.get<long long>(n);
+    cand.cs = A.get<long long>(n);
+    if (n) {
+      refine_loads(L, part, ctl, s);
+      refine_level_run(L, part, ctl, cand, s);
+    }
+    GP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (stats) {
+      stats[0] = hc.rounds;
+      stats[1] = hc.balanced;
+      stats[2] = hc.moves;
+      stats[3] = hc.bal_moves;
+      stats[4] = hc.LC;
+      stats[5] = hc.LG;
+    }
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,296 @@
+// gp_internal.cuh -- shared declarations of the CUDA implementation (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+
+#include "../../include/gp.h"
+
+namespace gp {
+
+// ------------------------------------------------------------------------------------------------
+// Fixed algorithm constants (they change results; the CPU oracle uses the same values).
+// ------------------------------------------------------------------------------------------------
+constexpr int kMatchRounds = 4;     // handshake rounds per coarsening level
+constexpr int kCapDiv = 8;          // merged vertex weight <= bound / 8
+constexpr int64_t kCoarsest = 128;  // stop coarsening at <= 128 vertices
+constexpr int kStallNum = 95;       // stop when a matching keeps > 95/100 of the vertices
+constexpr int kStallDen = 100;
+constexpr int kMaxLevels = GP_MAX_LEVELS;
+constexpr int kTrials = 8;          // greedy growing trials
+constexpr int kRefineRounds = 8;    // gain rounds per level
+constexpr int64_t kSumLimit = int64_t(1) << 61;
+constexpr int64_t kMaxN = (int64_t(1) << 31) - 2;
+
+// ------------------------------------------------------------------------------------------------
+// Kernel families (profiling / accounting ids).
+// ------------------------------------------------------------------------------------------------
+enum Family {
+  F_VALIDATE = 0, F_TRANSPOSE, F_LEVELS, F_SYM_MERGE, F_MATCH_PICK, F_MATCH_CONFIRM, F_TWOHOP,
+  F_CMAP, F_CONTRACT_MERGE, F_SCAN, F_GGGP, F_GAIN, F_SELECT, F_APPLY, F_PROJECT, F_MAKESPAN,
+  F_CUT, F_MISC, F_COUNT
+};
+extern const char* const kFamilyName[F_COUNT];
+
+// Device counters of algorithmic bytes per family (added by kernels, one atomic per block).  The
+// library is a single translation unit, so the definition lives here.
+__device__ unsigned long long d_alg_bytes[F_COUNT];
+
+// ------------------------------------------------------------------------------------------------
+// Launch bookkeeping (host).
+// ------------------------------------------------------------------------------------------------
+void launch_begin(int family, cudaStream_t s);
+void launch_end(int family, cudaStream_t s);
+bool prof_on();
+
+#define GP_LAUNCH(fam, kern, grid, block, smem, stream, ...)                  \
+  do {                                                                        \
+    ::gp::launch_begin((fam), (stream));                                      \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);                 \
+    ::gp::launch_end((fam), (stream));                                        \
+  } while (0)
+
+// cooperative launch helper; returns cudaError_t
+cudaError_t launch_coop(int family, const void* fn, int grid, int block, size_t smem, cudaStream_t s,
+                        void** args);
+
+// ------------------------------------------------------------------------------------------------
+// Error helpers.
+// ------------------------------------------------------------------------------------------------
+struct Fail {
+  gp_status st;
+};
+#define GP_CUDA(call)                                  \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) {                           \
+      if (e_ == cudaErrorMemoryAllocation) throw ::gp::Fail{GP_ERR_OOM}; \
+      throw ::gp::Fail{GP_ERR_CUDA};                   \
+    }                                                  \
+  } while (0)
+#define GP_CHECK_LAUNCH() GP_CUDA(cudaGetLastError())
+
+// stream-ordered allocation from the device pool
+void* dalloc(size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+template <class T>
+T* dnew(int64_t count, cudaStream_t s) {
+  return (T*)dalloc(sizeof(T) * (size_t)(count > 0 ? count : 1), s);
+}
+
+int num_sms();
+int device_id();
+
+// ------------------------------------------------------------------------------------------------
+// Device helpers.
+// ------------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+// tie-break hash of the unordered pair {a, b}, a = smaller id
+__host__ __device__ __forceinline__ uint64_t pair_hash(uint64_t seed, uint32_t a, uint32_t b) {
+  return mix64(seed ^ mix64(((uint64_t)a << 32) | (uint64_t)b));
+}
+
+// Edge key of the matching order: larger W first, then larger hash, then smaller (min, max).
+// `nm` holds ~((min << 32) | max) so that every component is "larger is better".
+struct EdgeKey {
+  int64_t W;
+  uint64_t h;
+  uint64_t nm;
+};
+__device__ __forceinline__ bool key_better(const EdgeKey& x, const EdgeKey& y) {
+  if (x.W != y.W) return x.W > y.W;
+  if (x.h != y.h) return x.h > y.h;
+  return x.nm > y.nm;
+}
+__device__ __forceinline__ EdgeKey key_none() { return EdgeKey{-1, 0, 0}; }
+__device__ __forceinline__ EdgeKey make_key(int64_t W, uint64_t seed, uint32_t v, uint32_t u) {
+  const uint32_t mn = v < u ? v : u, mx = v < u ? u : v;
+  return EdgeKey{W, pair_hash(seed, mn, mx), ~(((uint64_t)mn << 32) | (uint64_t)mx)};
+}
+__device__ __forceinline__ int32_t key_other(const EdgeKey& k, uint32_t v) {
+  const uint64_t mm = ~k.nm;
+  const uint32_t mn = (uint32_t)(mm >> 32), mx = (uint32_t)mm;
+  return (int32_t)(mn == v ? mx : mn);
+}
+__device__ __forceinline__ EdgeKey warp_best_key(EdgeKey k) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    EdgeKey q;
+    q.W = __shfl_xor_sync(0xffffffffu, k.W, o);
+    q.h = __shfl_xor_sync(0xffffffffu, k.h, o);
+    q.nm = __shfl_xor_sync(0xffffffffu, k.nm, o);
+    if (key_better(q, k)) k = q;
+  }
+  return k;
+}
+
+__device__ __forceinline__ int64_t warp_sum64(int64_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ unsigned long long warp_sumu64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Block-wide sum (all threads get the result).  `sh` needs 32 slots.
+template <class T>
+__device__ __forceinline__ T block_sum(T x, T* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  T t = (threadIdx.x < nw) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[0] = t;
+  }
+  __syncthreads();
+  T r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// accounting: add bytes to a family's counter once per block
+__device__ __forceinline__ void account(int fam, unsigned long long bytes_this_thread,
+                                        unsigned long long* sh) {
+  unsigned long long s = block_sum<unsigned long long>(bytes_this_thread, sh);
+  if (threadIdx.x == 0 && s) atomicAdd(&d_alg_bytes[fam], s);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Grid barrier for cooperative persistent kernels.  Bounded spin: after kSpinLimit polls the
+// waiting block records GP_ERR_TIMEOUT in *err and every block leaves its loop.
+// bar[0] = arrival counter, bar[1] = generation.
+// ------------------------------------------------------------------------------------------------
+constexpr long long kSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Returns false if the barrier timed out (or an earlier barrier did): callers must then return.
+// If snap_src is given, the last block to arrive copies *snap_src to *snap_dst before releasing the
+// others: a value that every block wrote to before arriving is then read consistently afterwards,
+// even while fast blocks already modify *snap_src again.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err,
+                                             const unsigned long long* snap_src = nullptr,
+                                             unsigned long long* snap_dst = nullptr) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = ld_acquire_i32(err) == 0;
+    if (ok) {
+      const unsigned gen = ld_acquire_u32(bar + 1);
+      __threadfence();
+      const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+      if (arrived == gridDim.x) {
+        if (snap_src) *(volatile unsigned long long*)snap_dst = atomicAdd((unsigned long long*)snap_src, 0ull);
+        atomicExch(bar, 0u);
+        __threadfence();
+        st_release_u32(bar + 1, gen + 1u);
+      } else {
+        long long spins = 0;
+        while (ld_acquire_u32(bar + 1) == gen) {
+          if (++spins > kSpinLimit || ld_acquire_i32(err) != 0) {
+            atomicCAS(err, 0, (int)GP_ERR_TIMEOUT);
+            ok = 0;
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Level graph in padded CSR: row v occupies [start[v], start[v] + deg[v]) of adj / W.
+// ------------------------------------------------------------------------------------------------
+struct LevelGraph {
+  int64_t n = 0;
+  int64_t cap = 0;       // capacity of adj / W
+  int64_t* start = nullptr;
+  int32_t* deg = nullptr;
+  int32_t* adj = nullptr;
+  int64_t* W = nullptr;
+  int64_t* vC = nullptr;
+  int64_t* vG = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------------
+// Host launchers (implemented in the k_*.cu files).
+// ------------------------------------------------------------------------------------------------
+
+// scans: exclusive prefix sum of in[0..n) into out[0..n], out[n] = total.  `total_host` may be NULL.
+void scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+void scan_u8_to_i32(const uint8_t* in, int32_t* out, int64_t n, cudaStream_t s);
+
+// row merge: for every row r of a "two-source" description, gather entries, map columns,
+// drop column == self_col(r), sort by column, add up equal columns, write at out_start[r].
+struct TwoSrc {
+  // row r takes entries from segment A = [a_beg[ra], a_beg[ra] + a_len(ra)) and optionally
+  // segment B, mapping column c -> map[c] when map != NULL.
+  const int64_t* a_start;  // per source row start
+  const int32_t* a_deg;    // per source row length (NULL: a_start[r+1] - a_start[r])
+  const int32_t* a_col;
+  const int32_t* a_w32;    // weights int32 (or NULL)
+  const int64_t* a_w64;    // weights int64 (or NULL)
+  const int64_t* b_start;
+  const int32_t* b_deg;
+  const int32_t* b_col;
+  const int32_t* b_w32;
+  const int64_t* b_w64;
+  const int32_t* row_a;    // source row of segment A for output row r (NULL: r)
+  const int32_t* row_b;    // source row of segment B (NULL: r); -1 = none
+  const int32_t* map;      // column map (NULL: identity)
+  int32_t drop_self;       // drop mapped column == r
+};
+// Writes deg_out[r] and the merged row at out_start[r] (capacity = raw length).
+// raw_bound >= total raw entries (sizes the scratch of the long-row tier).
+void merge_rows(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* out_start,
+                int32_t* deg_out, int32_t* adj_out, int64_t* W_out, int family, int64_t raw_bound,
+                cudaStream_t s);
+
+// coarsening
+void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, int rounds,
+                 bool twohop, int32_t* mate, cudaStream_t s);
+// rep flags + scan: cmap (partial) and number of coarse vertices written to *nc_dev
+void coarse_count(const LevelGraph& g, const int32_t* mate, int32_t* cmap, int64_t* nc_dev, cudaStream_t s);
+// fill the coarse level (requires cg.n set and arrays allocated with cg.cap = g's entry total)
+void contract_level(const LevelGraph& g, const int32_t* mate, int32_t* cmap, LevelGraph& cg,
+                    cudaStream_t s);
+
+// initial split
+void gggp(const LevelGraph& g, int64_t BC, int64_t BG, int64_t SG, uint64_t seed, uint8_t* part,
+          int32_t* trial_dev, cudaStream_t s);
+void gggp_grow_one(const LevelGraph& g, int64_t BC, int64_t BG, int64_t start, uint8_t* part,
+                   int64_t* cut_dev, cudaStream_t s);
+
+void project(int64_t n, const int32_t* cmap, const uint8_t* part_c, uint8_t* part_f, cudaStream_t s);
+
+}  // namespace gp

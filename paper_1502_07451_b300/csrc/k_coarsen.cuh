@@ -1,0 +1,294 @@
+// k_coarsen.cuh -- coarsening: handshake heavy-edge matching, two-hop pairing, contraction.
+//
+// Matching round (synchronous): every unmatched vertex v picks, among its unmatched neighbours u
+// whose merged weights stay within the caps, the edge with the largest key
+// (W desc, h(seed, min, max) desc, min asc, max asc); v and u match when they picked each other.
+// Two-hop pairing: each vertex still unmatched names its best neighbour under the same key (its
+// anchor); walking each anchor's row in ascending neighbour order, consecutive anchored vertices
+// are paired unless their merged weights exceed the caps (a failed pair leaves the newer one
+// pending).  Contraction: representatives (unmatched vertices and the smaller end of each pair)
+// are numbered in vertex order; a coarse row is the union of both members' rows mapped through
+// cmap, without the coarse vertex itself, equal neighbours added up.
+#pragma once
+#include "gp_internal.cuh"
+#include "k_graph.cuh"
+#include "k_rows.cuh"
+#include "k_scan.cuh"
+
+namespace gp {
+
+__global__ void k_match_init(int64_t n, const int64_t* __restrict__ vC, const int64_t* __restrict__ vG,
+                             int64_t capC, int64_t capG, int32_t* __restrict__ mate,
+                             int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    mate[v] = -1;
+    pick[v] = -1;
+    // a vertex over a cap on its own can never merge (weights are >= 0)
+    alive[v] = (vC[v] <= capC && vG[v] <= capG) ? 1 : 0;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const int32_t* __restrict__ mate,
+                 int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t v = gw; v < g.n; v += nw) {
+    if (lane == 0) bytes += 5;
+    if (mate[v] != -1 || !alive[v]) continue;
+    const int64_t b = g.start[v];
+    const int32_t d = g.deg[v];
+    const int64_t cv = g.vC[v], gv = g.vG[v];
+    EdgeKey best = key_none();
+    for (int32_t k = lane; k < d; k += 32) {
+      const int32_t u = g.adj[b + k];
+      bytes += 8;
+      if (mate[u] != -1) continue;
+      const int64_t cu = g.vC[u], gu = g.vG[u];
+      bytes += 24;
+      if (cv + cu > capC || gv + gu > capG) continue;
+      const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)u);
+      if (key_better(kk, best)) best = kk;
+    }
+    best = warp_best_key(best);
+    if (lane == 0) {
+      bytes += 12 + 16 + 4;
+      if (best.W < 0) {
+        pick[v] = -1;
+        alive[v] = 0;  // no eligible neighbour now means none later: neighbours only get matched
+      } else {
+        pick[v] = key_other(best, (uint32_t)v);
+      }
+    }
+  }
+  account(F_MATCH_PICK, bytes, sacc);
+}
+
+__global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (mate[v] != -1) continue;
+    const int32_t u = pick[v];
+    if (u >= 0 && pick[u] == (int32_t)v) mate[v] = u;
+  }
+}
+
+// anchor of every unmatched vertex: its best neighbour under the matching key (no filters)
+__global__ void __launch_bounds__(256)
+    k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
+             uint8_t* __restrict__ is_anchor) {
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t v = gw; v < g.n; v += nw) {
+    if (mate[v] != -1) {
+      if (lane == 0) {
+        anchor[v] = -1;
+        bytes += 8;
+      }
+      continue;
+    }
+    const int64_t b = g.start[v];
+    const int32_t d = g.deg[v];
+    EdgeKey best = key_none();
+    for (int32_t k = lane; k < d; k += 32) {
+      const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)g.adj[b + k]);
+      if (key_better(kk, best)) best = kk;
+      bytes += 12;
+    }
+    best = warp_best_key(best);
+    if (lane == 0) {
+      bytes += 20;
+      if (best.W < 0) {
+        anchor[v] = -1;
+      } else {
+        const int32_t a = key_other(best, (uint32_t)v);
+        anchor[v] = a;
+        is_anchor[a] = 1;
+      }
+    }
+  }
+  account(F_TWOHOP, bytes, sacc);
+}
+
+// Pairs the vertices anchored at h in ascending neighbour order.  Sequentially: a vertex joins the
+// pending one when the caps allow (pair formed, nothing pending), else it becomes pending.  With
+// P_i = "item i is pending after its turn" and ok_i = "caps allow item i-1 with item i":
+// P_i = !(P_{i-1} && ok_i), so P flips along runs of ok and resets to true where ok fails; item i is
+// paired with item i-1 exactly when P_i is false.  A warp evaluates this 32 row entries at a time
+// with a max-scan of the last reset position, carrying the last item across chunks.
+__global__ void __launch_bounds__(256)
+    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
+             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate) {
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  for (int64_t h = gw; h < g.n; h += nw) {
+    if (!is_anchor[h]) continue;
+    const int64_t b = g.start[h];
+    const int32_t d = g.deg[h];
+    int32_t p_id = -1;  // carried last item (any earlier chunk)
+    int64_t p_c = 0, p_g = 0;
+    bool p_pend = false;
+    for (int32_t base = 0; base < d; base += 32) {
+      const int32_t k = base + lane;
+      int32_t v = -1;
+      bool flag = false;
+      if (k < d) {
+        v = g.adj[b + k];
+        flag = anchor[v] == (int32_t)h;
+        bytes += 8;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, flag);
+      if (m == 0) continue;
+      int64_t vc = 0, vg = 0;
+      if (flag) {
+        vc = g.vC[v];
+        vg = g.vG[v];
+        bytes += 16;
+      }
+      const unsigned below = m & lt;
+      const int pred_lane = below ? 31 - __clz(below) : -1;
+      const int srcl = pred_lane >= 0 ? pred_lane : lane;
+      int32_t q_id = __shfl_sync(0xffffffffu, v, srcl);
+      int64_t q_c = __shfl_sync(0xffffffffu, vc, srcl);
+      int64_t q_g = __shfl_sync(0xffffffffu, vg, srcl);
+      if (pred_lane < 0) {
+        q_id = p_id;
+        q_c = p_c;
+        q_g = p_g;
+      }
+      const bool okprev = flag && q_id >= 0 && (q_c + vc <= capC) && (q_g + vg <= capG);
+      const int sidx = __popc(below);
+      int scan = (flag && !okprev) ? sidx : INT_MIN;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, scan, o);
+        if (lane >= o) scan = y > scan ? y : scan;
+      }
+      const int r0 = (p_id >= 0 && p_pend) ? -1 : -2;
+      const int lr = scan > r0 ? scan : r0;
+      const bool P = ((sidx - lr) & 1) == 0;
+      if (flag && !P) {
+        mate[v] = q_id;
+        mate[q_id] = v;
+        bytes += 8;
+      }
+      const int last = 31 - __clz(m);
+      p_id = __shfl_sync(0xffffffffu, v, last);
+      p_c = __shfl_sync(0xffffffffu, vc, last);
+      p_g = __shfl_sync(0xffffffffu, vg, last);
+      p_pend = __shfl_sync(0xffffffffu, P, last);
+    }
+  }
+  account(F_TWOHOP, bytes, sacc);
+}
+
+__global__ void k_rep_flags(int64_t n, const int32_t* __restrict__ mate, uint8_t* __restrict__ rep) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = mate[v];
+    rep[v] = (u < 0 || v < u) ? 1 : 0;
+  }
+}
+
+// cmap holds the exclusive scan of the representative flags; complete it and set up the coarse
+// vertices: members, summed weights, raw row length.
+__global__ void k_cmap_fill(LevelGraph g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
+                            int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of,
+                            int64_t* __restrict__ cvC, int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = mate[v];
+    if (u < 0 || v < u) {
+      const int32_t c = cmap[v];
+      rep_of[c] = (int32_t)v;
+      mate_of[c] = u;
+      cvC[c] = g.vC[v] + (u >= 0 ? g.vC[u] : 0);
+      cvG[c] = g.vG[v] + (u >= 0 ? g.vG[u] : 0);
+      rawlen[c] = (int64_t)g.deg[v] + (u >= 0 ? (int64_t)g.deg[u] : 0);
+    } else {
+      cmap[v] = cmap[u];
+    }
+  }
+}
+
+static inline unsigned grid_for(int64_t work, int per_block, int max_per_sm = 16) {
+  const int64_t want = (work + per_block - 1) / per_block;
+  const int64_t cap = (int64_t)num_sms() * max_per_sm;
+  return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, int rounds, bool twohop,
+                 int32_t* mate, cudaStream_t s) {
+  const int64_t n = g.n;
+  if (n <= 0) return;
+  int32_t* pick = dnew<int32_t>(n, s);
+  uint8_t* alive = dnew<uint8_t>(n, s);
+  GP_LAUNCH(F_MISC, k_match_init, grid_for(n, 256), 256, 0, s, n, g.vC, g.vG, capC, capG, mate, pick, alive);
+  for (int r = 0; r < rounds; r++) {
+    GP_LAUNCH(F_MATCH_PICK, k_match_pick, grid_for(n * 32, 256), 256, 0, s, g, capC, capG, seed, mate, pick,
+              alive);
+    GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick);
+  }
+  if (twohop) {
+    int32_t* anchor = pick;  // reuse
+    uint8_t* is_anchor = alive;
+    GP_CUDA(cudaMemsetAsync(is_anchor, 0, (size_t)n, s));
+    GP_LAUNCH(F_TWOHOP, k_anchor, grid_for(n * 32, 256), 256, 0, s, g, seed, mate, anchor, is_anchor);
+    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n * 32, 256), 256, 0, s, g, capC, capG, anchor, is_anchor, mate);
+  }
+  GP_CHECK_LAUNCH();
+  dfree(pick, s);
+  dfree(alive, s);
+}
+
+void coarse_count(const LevelGraph& g, const int32_t* mate, int32_t* cmap, int64_t* /*unused*/, cudaStream_t s) {
+  const int64_t n = g.n;
+  uint8_t* rep = dnew<uint8_t>(n, s);
+  GP_LAUNCH(F_CMAP, k_rep_flags, grid_for(n, 256), 256, 0, s, n, mate, rep);
+  scan_u8_to_i32(rep, cmap, n, s);  // cmap[n] = number of coarse vertices
+  dfree(rep, s);
+}
+
+// Requires cg.n = number of coarse vertices and cg.cap >= sum of the fine degrees; allocates the
+// coarse arrays.
+void contract_level(const LevelGraph& g, const int32_t* mate, int32_t* cmap, LevelGraph& cg, cudaStream_t s) {
+  const int64_t nc = cg.n;
+  int32_t* rep_of = dnew<int32_t>(nc, s);
+  int32_t* mate_of = dnew<int32_t>(nc, s);
+  int64_t* rawlen = dnew<int64_t>(nc, s);
+  cg.start = dnew<int64_t>(nc + 1, s);
+  cg.deg = dnew<int32_t>(nc, s);
+  cg.vC = dnew<int64_t>(nc, s);
+  cg.vG = dnew<int64_t>(nc, s);
+  cg.adj = dnew<int32_t>(cg.cap, s);
+  cg.W = dnew<int64_t>(cg.cap, s);
+  GP_LAUNCH(F_CMAP, k_cmap_fill, grid_for(g.n, 256), 256, 0, s, g, mate, cmap, rep_of, mate_of, cg.vC, cg.vG,
+            rawlen);
+  scan_i64(rawlen, cg.start, nc, s);
+  TwoSrc src{};
+  src.a_start = g.start;
+  src.a_deg = g.deg;
+  src.a_col = g.adj;
+  src.a_w64 = g.W;
+  src.b_start = g.start;
+  src.b_deg = g.deg;
+  src.b_col = g.adj;
+  src.b_w64 = g.W;
+  src.row_a = rep_of;
+  src.row_b = mate_of;
+  src.map = cmap;
+  src.drop_self = 1;
+  merge_rows(src, nc, nc, cg.start, cg.deg, cg.adj, cg.W, F_CONTRACT_MERGE, cg.cap, s);
+  dfree(rep_of, s);
+  dfree(mate_of, s);
+  dfree(rawlen, s);
+}
+
+}  // namespace gp

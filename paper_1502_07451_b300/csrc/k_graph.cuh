@@ -1,0 +1,227 @@
+// k_graph.cuh -- graph creation: validation, transpose, topological levels, symmetrisation inputs.
+#pragma once
+#include "gp_internal.cuh"
+#include "k_scan.cuh"
+
+namespace gp {
+
+enum : int { VF_INVALID = 1, VF_SELFLOOP = 2 };
+
+// 64-bit add into a 128-bit (lo, hi) accumulator.
+__device__ __forceinline__ void add_u128(unsigned long long* acc, unsigned long long x) {
+  if (x == 0) return;
+  const unsigned long long old = atomicAdd(acc, x);
+  if (old + x < old) atomicAdd(acc + 1, 1ull);
+}
+
+// Checks offsets, ids, costs; sums edge / CPU / GPU costs into sums[0..5] (three 128-bit values).
+__global__ void __launch_bounds__(256)
+    k_validate(int64_t n, int64_t m, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+               const int32_t* __restrict__ w, const int32_t* __restrict__ cC,
+               const int32_t* __restrict__ cG, int* flags, unsigned long long* sums) {
+  __shared__ unsigned long long sh[32];
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int bad = 0;
+  unsigned long long sw = 0, sc = 0, sg = 0;
+  if (tid == 0 && (off[0] != 0 || off[n] != m)) bad = 1;
+  for (int64_t v = tid; v < n; v += stride) {
+    if (off[v + 1] < off[v]) bad = 1;
+    const int32_t a = cC[v], b = cG[v];
+    if (a < 0 || b < 0) bad = 1;
+    sc += (unsigned long long)(a < 0 ? 0 : a);
+    sg += (unsigned long long)(b < 0 ? 0 : b);
+  }
+  for (int64_t e = tid; e < m; e += stride) {
+    const int32_t c = cols[e], x = w[e];
+    if (c < 0 || c >= n || x < 0) bad = 1;
+    sw += (unsigned long long)(x < 0 ? 0 : x);
+  }
+  if (bad) atomicOr(flags, VF_INVALID);
+  sw = block_sum<unsigned long long>(sw, sh);
+  sc = block_sum<unsigned long long>(sc, sh);
+  sg = block_sum<unsigned long long>(sg, sh);
+  if (threadIdx.x == 0) {
+    add_u128(sums + 0, sw);
+    add_u128(sums + 2, sc);
+    add_u128(sums + 4, sg);
+  }
+}
+
+__global__ void k_indeg(int64_t m, const int32_t* __restrict__ cols, int32_t* __restrict__ indeg) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&indeg[cols[e]], 1);
+}
+
+// in-CSR fill (warp per source row); also detects self-loops
+__global__ void __launch_bounds__(256)
+    k_fill_in(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+              const int32_t* __restrict__ w, const int64_t* __restrict__ in_off, int32_t* cursor,
+              int32_t* __restrict__ in_src, int32_t* __restrict__ in_w, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = gw; u < n; u += nw) {
+    const int64_t b = off[u], e_end = off[u + 1];
+    for (int64_t e = b + lane; e < e_end; e += 32) {
+      const int32_t v = cols[e];
+      if (v == (int32_t)u) atomicOr(flags, VF_SELFLOOP);
+      const int64_t pos = in_off[v] + atomicAdd(&cursor[v], 1);
+      in_src[pos] = (int32_t)u;
+      in_w[pos] = w[e];
+    }
+  }
+}
+
+// Kahn's algorithm, level-synchronous, in one cooperative launch.  Level l holds the vertices whose
+// longest path from a source has l edges: lev_vtx[lev_ptr[l] .. lev_ptr[l+1]).
+__global__ void __launch_bounds__(256)
+    k_levels(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+             const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int64_t* lev_ptr,
+             int32_t* level, unsigned long long* tail, int32_t* nlev_out, unsigned* bar, int* err) {
+  // tail: next free slot of lev_vtx (appends); tail + 1: its value when the last barrier released
+  const int lane = threadIdx.x & 31;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gw = tid >> 5, nw = stride >> 5;
+  for (int64_t v = tid; v < n; v += stride) {
+    const int32_t d = (int32_t)(in_off[v + 1] - in_off[v]);
+    rem[v] = d;
+    if (d == 0) {
+      const unsigned long long pos = atomicAdd(tail, 1ull);
+      lev_vtx[pos] = (int32_t)v;
+      level[v] = 0;
+    }
+  }
+  if (!grid_barrier(bar, err, tail, tail + 1)) return;
+  int64_t beg = 0, end = (int64_t) * (volatile unsigned long long*)(tail + 1);
+  int32_t lev = 0;
+  while (end > beg) {
+    if (tid == 0) lev_ptr[lev] = beg;
+    for (int64_t i = beg + gw; i < end; i += nw) {
+      const int32_t v = __ldcg(lev_vtx + i);  // written by other blocks: bypass L1
+      const int64_t eb = off[v], ee = off[v + 1];
+      for (int64_t e = eb + lane; e < ee; e += 32) {
+        const int32_t u = cols[e];
+        if (atomicSub(&rem[u], 1) == 1) {
+          const unsigned long long pos = atomicAdd(tail, 1ull);
+          lev_vtx[pos] = u;
+          level[u] = lev + 1;
+        }
+      }
+    }
+    if (!grid_barrier(bar, err, tail, tail + 1)) return;
+    beg = end;
+    end = (int64_t) * (volatile unsigned long long*)(tail + 1);
+    lev++;
+  }
+  if (tid == 0) {
+    lev_ptr[lev] = beg;
+    *nlev_out = lev;
+  }
+}
+
+// position i of the level order: vertex, in-degree, costs
+__global__ void k_lo_prep(int64_t n, const int32_t* __restrict__ lev_vtx, const int64_t* __restrict__ in_off,
+                          const int32_t* __restrict__ cC, const int32_t* __restrict__ cG,
+                          int32_t* __restrict__ pos_of, int32_t* __restrict__ lo_deg,
+                          int32_t* __restrict__ lo_cC, int32_t* __restrict__ lo_cG) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = lev_vtx[i];
+    pos_of[v] = (int32_t)i;
+    lo_deg[i] = (int32_t)(in_off[v + 1] - in_off[v]);
+    lo_cC[i] = cC[v];
+    lo_cG[i] = cG[v];
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_lo_fill(int64_t n, const int32_t* __restrict__ lev_vtx, const int64_t* __restrict__ in_off,
+              const int32_t* __restrict__ in_src, const int32_t* __restrict__ in_w,
+              const int32_t* __restrict__ pos_of, const int64_t* __restrict__ lo_off,
+              int32_t* __restrict__ lo_src, int32_t* __restrict__ lo_w) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n; i += nw) {
+    const int32_t v = lev_vtx[i];
+    const int64_t b = in_off[v], d = in_off[v + 1] - b, o = lo_off[i];
+    for (int64_t k = lane; k < d; k += 32) {
+      lo_src[o + k] = pos_of[in_src[b + k]];
+      lo_w[o + k] = in_w[b + k];
+    }
+  }
+}
+
+__global__ void k_rawlen_sym(int64_t n, const int64_t* __restrict__ off, const int64_t* __restrict__ in_off,
+                             int64_t* __restrict__ rawlen) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    rawlen[v] = (off[v + 1] - off[v]) + (in_off[v + 1] - in_off[v]);
+}
+
+__global__ void k_widen(int64_t n, const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                        int64_t* __restrict__ wa, int64_t* __restrict__ wb) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    wa[v] = a[v];
+    wb[v] = b[v];
+  }
+}
+
+__global__ void k_sum_deg(int64_t n, const int32_t* __restrict__ deg, unsigned long long* out) {
+  __shared__ unsigned long long sh[32];
+  unsigned long long s = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)deg[v];
+  s = block_sum<unsigned long long>(s, sh);
+  if (threadIdx.x == 0 && s) atomicAdd(out, s);
+}
+
+__global__ void k_sum_i64(int64_t n, const int64_t* __restrict__ x, unsigned long long* out) {
+  __shared__ unsigned long long sh[32];
+  unsigned long long s = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    s += (unsigned long long)x[v];
+  s = block_sum<unsigned long long>(s, sh);
+  if (threadIdx.x == 0 && s) atomicAdd(out, s);
+}
+
+// sum of non-negative int64 values into *out (zeroed here)
+void sum_i64(const int64_t* x, int64_t n, long long* out, cudaStream_t s) {
+  GP_CUDA(cudaMemsetAsync(out, 0, sizeof(long long), s));
+  const int64_t want = (n + 255) / 256;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  GP_LAUNCH(F_MISC, k_sum_i64, (unsigned)(want < 1 ? 1 : (want < cap ? want : cap)), 256, 0, s, n, x,
+            (unsigned long long*)out);
+  GP_CHECK_LAUNCH();
+}
+
+// padded CSR -> compact CSR copy (warp per row); coff must hold the exclusive scan of deg
+__global__ void __launch_bounds__(256)
+    k_compact_rows(int64_t n, const int64_t* __restrict__ start, const int32_t* __restrict__ deg,
+                   const int32_t* __restrict__ adj, const int64_t* __restrict__ W,
+                   const int64_t* __restrict__ coff, int32_t* __restrict__ cadj, int64_t* __restrict__ cW) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = gw; v < n; v += nw) {
+    const int64_t b = start[v], o = coff[v];
+    const int32_t d = deg[v];
+    for (int32_t k = lane; k < d; k += 32) {
+      cadj[o + k] = adj[b + k];
+      cW[o + k] = W[b + k];
+    }
+  }
+}
+
+// compact CSR -> (start, deg) view
+__global__ void k_deg_from_off(int64_t n, const int64_t* __restrict__ off, int32_t* __restrict__ deg) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    deg[v] = (int32_t)(off[v + 1] - off[v]);
+}
+
+__global__ void k_fill_u8(int64_t n, uint8_t* p, uint8_t x) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    p[v] = x;
+}
+
+}  // namespace gp

@@ -1,0 +1,450 @@
+// k_refine.cuh -- uncoarsening: projection, balance round, synchronous gain rounds.
+//
+// gain(v) = W(v, other side) - W(v, own side).  Gain round r moves vertices from side r mod 2: the
+// candidates are that side's vertices with gain > 0; in (gain desc, id asc) order, the longest
+// prefix whose added weight keeps the destination within its bound moves, all at once.  A balance
+// round (only when the split is infeasible) orders all of the over-bound side's vertices the same
+// way and moves the shortest prefix that brings that side within its bound while the other side
+// stays within its bound, else the longest prefix that keeps the other side within its bound.
+// Rounds stop after two consecutive rounds without moves.
+//
+// The ordered prefix is found without sorting: the candidates' keys
+// ((gmax - gain) << idbits | id, unique, ascending = gain desc, id asc) are radix-selected by
+// their cumulative weight (8-bit digits, most significant first) in one CTA.  All round control
+// lives in a device block (RefineCtl), so a level's rounds are enqueued without host round trips;
+// kernels of rounds after the stop return at once.
+#pragma once
+#include "gp_internal.cuh"
+#include "k_coarsen.cuh"
+
+namespace gp {
+
+typedef unsigned __int128 u128;
+
+struct CandCounters {
+  unsigned long long ncand;
+  unsigned long long cost_dst, cost_src;
+  long long gmax, gmin;
+};
+
+// device control block of one partition call
+struct Ctl {
+  long long BC, BG, LC, LG;
+  CandCounters cc[2];          // candidates of the current round, double-buffered by round parity
+  int32_t sel_round;           // round whose selection ran last (-1 balance, -2 none)
+  int32_t accept;              // 0 none, 1 all, 2 keys below thr
+  unsigned long long thr_hi, thr_lo;
+  long long sel_gmax;
+  int32_t idbits, side_src;
+  int32_t done, streak, rounds, balanced, bal_active, pad;
+  long long moves, bal_moves, take;
+};
+
+struct Cands {
+  int32_t* id;
+  long long* gain;
+  long long* cd;  // weight joining the destination
+  long long* cs;  // weight leaving the source
+};
+
+__device__ __forceinline__ u128 cand_key(long long gmax, long long gain, int32_t id, int idbits) {
+  return ((u128)(unsigned long long)(gmax - gain) << idbits) | (u128)(uint32_t)id;
+}
+
+__global__ void k_ref_loads(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl) {
+  __shared__ long long sh[32];
+  long long c = 0, gg = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (part[v] == 0)
+      c += g.vC[v];
+    else
+      gg += g.vG[v];
+  }
+  c = block_sum<long long>(c, sh);
+  gg = block_sum<long long>(gg, sh);
+  if (threadIdx.x == 0) {
+    if (c) atomicAdd((unsigned long long*)&ctl->LC, (unsigned long long)c);
+    if (gg) atomicAdd((unsigned long long*)&ctl->LG, (unsigned long long)gg);
+  }
+}
+
+__device__ __forceinline__ void reset_counters(CandCounters& c) {
+  c.ncand = 0;
+  c.cost_dst = 0;
+  c.cost_src = 0;
+  c.gmax = LLONG_MIN;
+  c.gmin = LLONG_MAX;
+}
+
+__global__ void k_ref_begin(Ctl* ctl, int idbits) {
+  Ctl& c = *ctl;
+  c.done = 0;
+  c.streak = 0;
+  c.rounds = 0;
+  c.balanced = 0;
+  c.moves = 0;
+  c.bal_moves = 0;
+  c.sel_round = -2;
+  c.idbits = idbits;
+  reset_counters(c.cc[0]);
+  reset_counters(c.cc[1]);
+  const bool overC = c.LC > c.BC, overG = c.LG > c.BG;
+  c.bal_active = (overC || overG) ? 1 : 0;
+  if (overC && overG) {
+    const __int128 lhs = (__int128)(c.LC - c.BC) * (__int128)c.BG;
+    const __int128 rhs = (__int128)(c.LG - c.BG) * (__int128)c.BC;
+    c.side_src = (lhs >= rhs) ? 0 : 1;
+  } else {
+    c.side_src = overC ? 0 : 1;
+  }
+}
+
+// r = -1: balance round, else gain round r.  Warp per 32 consecutive vertices.
+__global__ void __launch_bounds__(256)
+    k_ref_gain(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, Cands cand) {
+  __shared__ long long sh[32];
+  __shared__ unsigned long long shu[32];
+  __shared__ unsigned long long sacc[32];
+  __shared__ int s_src, s_skip;
+  if (threadIdx.x == 0) {
+    s_skip = (r < 0) ? !ctl->bal_active : ctl->done;
+    s_src = (r < 0) ? ctl->side_src : (r & 1);
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int src = s_src;
+  const int par = (r < 0) ? 1 : (r & 1);
+  CandCounters* cc = &ctl->cc[par];
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t* cdst = src == 0 ? g.vG : g.vC;
+  const int64_t* csrc = src == 0 ? g.vC : g.vG;
+  unsigned long long sum_cd = 0, sum_cs = 0, bytes = 0;
+  long long gmax = LLONG_MIN, gmin = LLONG_MAX;
+  for (int64_t base = gw * 32; base < g.n; base += nw * 32) {
+    const int64_t mv = base + lane;
+    const bool on = mv < g.n && part[mv] == src;
+    unsigned m = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) bytes += 32;
+    while (m) {
+      const int bit = __ffs(m) - 1;
+      m &= m - 1;
+      const int64_t v = base + bit;
+      const int64_t b = g.start[v];
+      const int32_t d = g.deg[v];
+      long long ext = 0, in = 0;
+      for (int32_t k = lane; k < d; k += 32) {
+        const int64_t w = g.W[b + k];
+        if (part[g.adj[b + k]] == src)
+          in += w;
+        else
+          ext += w;
+      }
+      const long long gain = warp_sum64(ext) - warp_sum64(in);
+      if (lane == 0) {
+        bytes += 12ull + 13ull * (unsigned long long)d;
+        if (r < 0 || gain > 0) {
+          const unsigned long long slot = atomicAdd(&cc->ncand, 1ull);
+          const long long a = cdst[v], c = csrc[v];
+          cand.id[slot] = (int32_t)v;
+          cand.gain[slot] = gain;
+          cand.cd[slot] = a;
+          cand.cs[slot] = c;
+          sum_cd += (unsigned long long)a;
+          sum_cs += (unsigned long long)c;
+          gmax = gain > gmax ? gain : gmax;
+          gmin = gain < gmin ? gain : gmin;
+          bytes += 16ull + 28ull;
+        }
+      }
+    }
+  }
+  sum_cd = block_sum<unsigned long long>(sum_cd, shu);
+  sum_cs = block_sum<unsigned long long>(sum_cs, shu);
+  // block max / min via warp shuffles then shared
+  {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long a = __shfl_xor_sync(0xffffffffu, gmax, o);
+      const long long b = __shfl_xor_sync(0xffffffffu, gmin, o);
+      gmax = a > gmax ? a : gmax;
+      gmin = b < gmin ? b : gmin;
+    }
+    if (lane == 0) sh[threadIdx.x >> 5] = gmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long mx = LLONG_MIN;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) mx = sh[w] > mx ? sh[w] : mx;
+      if (mx != LLONG_MIN) atomicMax(&cc->gmax, mx);
+    }
+    __syncthreads();
+    if (lane == 0) sh[threadIdx.x >> 5] = gmin;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long mn = LLONG_MAX;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) mn = sh[w] < mn ? sh[w] : mn;
+      if (mn != LLONG_MAX) atomicMin(&cc->gmin, mn);
+      if (sum_cd) atomicAdd(&cc->cost_dst, sum_cd);
+      if (sum_cs) atomicAdd(&cc->cost_src, sum_cs);
+    }
+  }
+  account(F_GAIN, bytes, sacc);
+}
+
+// Among the candidates in key order, the first one at which the running weight exceeds T (T >= 0).
+// which: 0 = destination weight, 1 = source weight, 2 = one per candidate.
+// Returns 1 and its key / rank (candidates with smaller keys) in shared memory, else 0.
+struct SelOut {
+  int found;
+  u128 key;
+  long long rank;
+};
+
+__device__ void block_select(const Cands& cand, unsigned long long N, int which, long long T, long long gmax,
+                             int idbits, int keybits, SelOut* out, unsigned long long* hw,
+                             unsigned long long* hc) {
+  __shared__ u128 s_prefix;
+  __shared__ long long s_T, s_rank;
+  __shared__ int s_found;
+  const int KB = ((keybits + 7) / 8) * 8;
+  if (threadIdx.x == 0) {
+    s_prefix = 0;
+    s_T = T;
+    s_rank = 0;
+    s_found = 1;
+  }
+  __syncthreads();
+  for (int shift = KB - 8; shift >= 0; shift -= 8) {
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+      hw[d] = 0;
+      hc[d] = 0;
+    }
+    __syncthreads();
+    const u128 prefix = s_prefix;
+    for (unsigned long long i = threadIdx.x; i < N; i += blockDim.x) {
+      const u128 k = cand_key(gmax, cand.gain[i], cand.id[i], idbits);
+      if ((k >> (shift + 8)) != prefix) continue;
+      const int d = (int)((k >> shift) & 255);
+      const unsigned long long w = which == 0 ? (unsigned long long)cand.cd[i]
+                                   : which == 1 ? (unsigned long long)cand.cs[i] : 1ull;
+      atomicAdd(&hw[d], w);
+      atomicAdd(&hc[d], 1ull);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long cum = 0;
+      int chosen = -1;
+      for (int d = 0; d < 256; d++) {
+        if (cum + (long long)hw[d] > s_T) {
+          chosen = d;
+          break;
+        }
+        cum += (long long)hw[d];
+        s_rank += (long long)hc[d];
+      }
+      if (chosen < 0) {
+        s_found = 0;
+      } else {
+        s_T -= cum;
+        s_prefix = (s_prefix << 8) | (u128)chosen;
+      }
+    }
+    __syncthreads();
+    if (!s_found) break;
+  }
+  if (threadIdx.x == 0) {
+    out->found = s_found;
+    out->key = s_prefix;
+    out->rank = s_rank;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int bits_of(unsigned long long x) {  // bits needed to hold x (>= 1)
+  return x == 0 ? 1 : 64 - __clzll((long long)x);
+}
+
+__global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, int64_t n, Cands cand) {
+  __shared__ unsigned long long hw[256], hc[256];
+  __shared__ SelOut so;
+  __shared__ int s_skip;
+  Ctl& c = *ctl;
+  if (threadIdx.x == 0) s_skip = (r < 0) ? !c.bal_active : c.done;
+  __syncthreads();
+  if (s_skip) return;
+  const int par = (r < 0) ? 1 : (r & 1);
+  const CandCounters cc = c.cc[par];
+  const unsigned long long N = cc.ncand;
+  const int idbits = c.idbits;
+  const long long gmax = cc.gmax;
+  const int keybits = N ? bits_of((unsigned long long)(cc.gmax - cc.gmin)) + idbits : 1;
+  long long k = 0;
+  int accept = 0;  // 0 none, 1 all, 2 below threshold
+  u128 thr = 0;
+  if (r >= 0) {
+    const int dst = 1 - (r & 1);
+    const long long Ld = dst == 0 ? c.LC : c.LG, Bd = dst == 0 ? c.BC : c.BG;
+    if (N == 0 || Ld > Bd) {
+      k = 0;
+    } else if ((long long)cc.cost_dst <= Bd - Ld) {
+      k = (long long)N;
+      accept = 1;
+    } else {
+      block_select(cand, N, 0, Bd - Ld, gmax, idbits, keybits, &so, hw, hc);
+      k = so.rank;
+      thr = so.key;
+      accept = k > 0 ? 2 : 0;
+    }
+  } else {
+    const int s = c.side_src;
+    const long long Ls = s == 0 ? c.LC : c.LG, Bs = s == 0 ? c.BC : c.BG;
+    const long long Lo = s == 0 ? c.LG : c.LC, Bo = s == 0 ? c.BG : c.BC;
+    const long long E = Ls - Bs;  // > 0
+    const long long INF = LLONG_MAX;
+    long long k1 = INF, k2;
+    if ((long long)cc.cost_src >= E && N > 0) {
+      block_select(cand, N, 1, E - 1, gmax, idbits, keybits, &so, hw, hc);
+      k1 = so.rank + 1;
+    }
+    const long long T2 = Bo - Lo;
+    if (T2 < 0) {
+      k2 = -1;
+    } else if ((long long)cc.cost_dst <= T2) {
+      k2 = (long long)N;
+    } else {
+      block_select(cand, N, 0, T2, gmax, idbits, keybits, &so, hw, hc);
+      k2 = so.rank;
+    }
+    k = (k1 <= k2) ? k1 : (k2 > 0 ? k2 : 0);
+    if (k == 0) {
+      accept = 0;
+    } else if (k == (long long)N) {
+      accept = 1;
+    } else {
+      block_select(cand, N, 2, k, gmax, idbits, keybits, &so, hw, hc);  // the candidate of rank k
+      thr = so.key;
+      accept = 2;
+    }
+  }
+  if (threadIdx.x == 0) {
+    c.sel_round = r;
+    c.accept = accept;
+    c.thr_hi = (unsigned long long)(thr >> 64);
+    c.thr_lo = (unsigned long long)thr;
+    c.sel_gmax = gmax;
+    c.take = k;
+    if (r >= 0) {
+      c.rounds += 1;
+      c.moves += k;
+      c.streak = (k == 0) ? c.streak + 1 : 0;
+      if (c.streak == 2) c.done = 1;
+      reset_counters(c.cc[par ^ 1]);  // the next round's counters (last read by round r-1)
+    } else {
+      c.balanced = 1;
+      c.bal_moves = k;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    k_ref_apply(Ctl* ctl, int r, uint8_t* __restrict__ part, const int64_t* __restrict__ vC,
+                const int64_t* __restrict__ vG, Cands cand) {
+  __shared__ long long sh[32];
+  __shared__ unsigned long long sacc[32];
+  __shared__ int s_go;
+  __shared__ int s_accept, s_src, s_idbits;
+  __shared__ unsigned long long s_N, s_hi, s_lo;
+  __shared__ long long s_gmax;
+  if (threadIdx.x == 0) {
+    const Ctl& c = *ctl;
+    s_go = (c.sel_round == r) && c.accept != 0;
+    s_accept = c.accept;
+    s_src = (r < 0) ? c.side_src : (r & 1);
+    s_idbits = c.idbits;
+    s_N = c.cc[(r < 0) ? 1 : (r & 1)].ncand;
+    s_hi = c.thr_hi;
+    s_lo = c.thr_lo;
+    s_gmax = c.sel_gmax;
+  }
+  __syncthreads();
+  if (!s_go) return;
+  const int dst = 1 - s_src;
+  const u128 thr = ((u128)s_hi << 64) | (u128)s_lo;
+  long long dC = 0, dG = 0;
+  unsigned long long bytes = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < s_N;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const int32_t v = cand.id[i];
+    bytes += 12;
+    if (s_accept == 2 && !(cand_key(s_gmax, cand.gain[i], v, s_idbits) < thr)) continue;
+    part[v] = (uint8_t)dst;
+    const long long c = vC[v], gg = vG[v];
+    bytes += 17;
+    if (dst == 1) {
+      dC -= c;
+      dG += gg;
+    } else {
+      dC += c;
+      dG -= gg;
+    }
+  }
+  dC = block_sum<long long>(dC, sh);
+  dG = block_sum<long long>(dG, sh);
+  if (threadIdx.x == 0) {
+    if (dC) atomicAdd((unsigned long long*)&ctl->LC, (unsigned long long)dC);
+    if (dG) atomicAdd((unsigned long long*)&ctl->LG, (unsigned long long)dG);
+  }
+  account(F_APPLY, bytes, sacc);
+}
+
+// per-level record: rounds, moves, balanced, balance moves
+__global__ void k_ref_end(const Ctl* ctl, int level, int32_t* t_rounds, long long* t_moves, int32_t* t_bal,
+                          long long* t_balmoves) {
+  t_rounds[level] = ctl->rounds;
+  t_moves[level] = ctl->moves;
+  t_bal[level] = ctl->balanced;
+  t_balmoves[level] = ctl->bal_moves;
+}
+
+__global__ void k_project(int64_t n, const int32_t* __restrict__ cmap, const uint8_t* __restrict__ pc,
+                          uint8_t* __restrict__ pf) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    pf[v] = pc[cmap[v]];
+}
+
+static inline int idbits_for(int64_t n) {
+  int b = 1;
+  while (b < 31 && (int64_t(1) << b) < n) b++;
+  return b;
+}
+
+void project(int64_t n, const int32_t* cmap, const uint8_t* part_c, uint8_t* part_f, cudaStream_t s) {
+  GP_LAUNCH(F_PROJECT, k_project, grid_for(n, 256), 256, 0, s, n, cmap, part_c, part_f);
+  GP_CHECK_LAUNCH();
+}
+
+// zero LC / LG and recompute them from part
+void refine_loads(const LevelGraph& g, const uint8_t* part, Ctl* ctl, cudaStream_t s) {
+  GP_CUDA(cudaMemsetAsync(&ctl->LC, 0, 2 * sizeof(long long), s));
+  GP_LAUNCH(F_MISC, k_ref_loads, grid_for(g.n, 256, 4), 256, 0, s, g, part, ctl);
+  GP_CHECK_LAUNCH();
+}
+
+void refine_level_run(const LevelGraph& g, uint8_t* part, Ctl* ctl, const Cands& cand, cudaStream_t s) {
+  const int64_t n = g.n;
+  const unsigned ggrid = grid_for((n + 31) / 32 * 32, 256);
+  const unsigned agrid = grid_for(n, 256, 4);
+  GP_LAUNCH(F_MISC, k_ref_begin, 1, 1, 0, s, ctl, idbits_for(n));
+  GP_LAUNCH(F_GAIN, k_ref_gain, ggrid, 256, 0, s, g, part, ctl, -1, cand);
+  GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, -1, n, cand);
+  GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, -1, part, g.vC, g.vG, cand);
+  for (int r = 0; r < kRefineRounds; r++) {
+    GP_LAUNCH(F_GAIN, k_ref_gain, ggrid, 256, 0, s, g, part, ctl, r, cand);
+    GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, r, n, cand);
+    GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, r, part, g.vC, g.vG, cand);
+  }
+  GP_CHECK_LAUNCH();
+}
+
+}  // namespace gp
