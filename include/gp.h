@@ -148,6 +148,27 @@ GP_API gp_status gp_last_trace(const gp_graph* g, gp_trace* trace);
 GP_API gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan, int64_t* finish_out,
                       void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * gp_makespan_noalloc -- the same result as gp_makespan, for callers that cannot allocate device
+ * memory (the paper has no counterpart: this is a deployment variant).  gp_makespan takes its
+ * per-call scratch from the device memory pool; callers that run inside a stream capture that
+ * forbids allocation, in latency-critical loops, or under a host allocator that owns all device
+ * memory cannot let it.  This variant uses a scratch array compiled into the library (8 MiB + 64
+ * bytes per GPU that loads the library, held until the process exits) and allocates nothing.
+ *   g           handle on the current device (GP_ERR_INVALID otherwise)
+ *   part        uint8[n] in DEVICE memory (0/1)
+ *   makespan    host int64, receives the result
+ *   finish_out  int64[n] in DEVICE memory, or NULL
+ * Limits: n <= GP_MAKESPAN_NOALLOC_MAX_N, else GP_ERR_INVALID before any work.  All calls on a GPU
+ * share the one scratch array: calls whose work overlaps on that GPU (other streams or threads)
+ * race; serialise them.  The first call on each device looks up the array's device address;
+ * make that first call before any stream capture begins.
+ * Errors: GP_ERR_INVALID (limits, host pointers, part[v] > 1), GP_ERR_CUDA, GP_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------------------------- */
+#define GP_MAKESPAN_NOALLOC_MAX_N (1 << 20)
+GP_API gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part, int64_t* makespan,
+                                     int64_t* finish_out, void* stream);
+
 /* Cut of a split: sum of edge costs of directed edges whose ends are on different sides. */
 GP_API gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* stream);
 

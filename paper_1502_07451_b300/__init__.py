@@ -86,6 +86,7 @@ def lib():
                 "gp_last_trace": [_P, _P],
                 "gp_makespan": [_P, _P, _P, _P, _P],
                 "gp_cut": [_P, _P, _P, _P],
+                "gp_makespan_noalloc": [_P, _P, _P, _P, _P],
                 "gp_step_match": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _I32, _I32, _P, _P],
                 "gp_step_contract": [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
                 "gp_step_gggp": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _P, _P, _P],
@@ -212,6 +213,26 @@ def gp_last_trace(h):
 def gp_makespan(h, part, finish_out=None, stream=None):
     ms = C.c_int64()
     _check(lib().gp_makespan(h, _ptr(part)[0], C.byref(ms), _ptr(finish_out)[0], _stream(stream)), "gp_makespan")
+    return int(ms.value)
+
+
+MAKESPAN_NOALLOC_MAX_N = 1 << 20
+
+
+def gp_makespan_noalloc(h, part, finish_out=None, stream=None):
+    """gp_makespan without any device allocation (scratch compiled into the library).
+
+    For callers that cannot allocate device memory.  ``part`` and ``finish_out`` must be device
+    tensors; at most MAKESPAN_NOALLOC_MAX_N vertices; calls that overlap on one GPU race on the
+    shared scratch.  The first call on a device resolves the scratch address: make it before any
+    stream capture.
+    """
+    ms = C.c_int64()
+    st = lib().gp_makespan_noalloc(h, _ptr(part)[0], C.byref(ms), _ptr(finish_out)[0], _stream(stream))
+    if st == GP_ERR_INVALID:
+        raise GpError(st, "gp_makespan_noalloc (device buffers required, at most %d vertices, handle on the "
+                          "current device)" % MAKESPAN_NOALLOC_MAX_N)
+    _check(st, "gp_makespan_noalloc")
     return int(ms.value)
 
 

@@ -933,3 +933,6 @@ gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, cons
 }
 
 }  // extern "C"
+
+// the no-allocation makespan variant (its scratch array must share this translation unit)
+#include "gp_noalloc.cu"
