@@ -40,7 +40,7 @@ typedef enum gp_status {
   GP_ERR_NOT_DAG = 2,  /* the graph has a cycle (a self-loop counts as one)               */
   GP_ERR_OOM = 3,      /* a device or host allocation failed                              */
   GP_ERR_CUDA = 4,     /* a CUDA runtime call or kernel launch failed                     */
-  GP_ERR_TIMEOUT = 5,  /* a device-side wait (grid barrier) exceeded its iteration limit  */
+  GP_ERR_TIMEOUT = 5,  /* a device-side wait exceeded its iteration limit (reserved)       */
   GP_ERR_OVERFLOW = 6  /* a summed cost exceeds 2^61 ns                                   */
 } gp_status;
 

@@ -90,12 +90,38 @@ static void prof_collect() {
   g_ev.clear();
 }
 
-cudaError_t launch_coop(int family, const void* fn, int grid, int block, size_t smem, cudaStream_t s,
-                        void** args) {
-  launch_begin(family, s);
-  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
-  launch_end(family, s);
-  return e;
+int cluster_max(const void* fn, int block) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> cache;  // ((fn, device), size)
+  const int dev = device_id();
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& c : cache)
+    if (c.first.first == fn && c.first.second == dev) return c.second;
+  int best = 0;
+  for (int cs : {16, 8, 4, 2, 1}) {
+    if (cs > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)cs);
+    cfg.blockDim = dim3((unsigned)block);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) == cudaSuccess && nclusters >= 1) {
+      best = cs;
+      break;
+    }
+    cudaGetLastError();
+  }
+  cache.push_back({{fn, dev}, best});
+  return best;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -161,12 +187,6 @@ struct Arena {
     for (void* p : ptrs) cudaFreeAsync(p, s);
   }
 };
-
-static int coop_blocks_per_sm(const void* fn, int block, size_t smem) {
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, block, smem) != cudaSuccess) return 1;
-  return b > 0 ? b : 1;
-}
 
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
@@ -250,6 +270,29 @@ static void graph_free(gp_graph* g) {
   for (void* p : g->owned) cudaFree(p);
   cudaSetDevice(cur);
   delete g;
+}
+
+// The makespan kernel in one cluster sized to the widest level (G lanes per vertex).
+static cudaError_t launch_makespan(const gp_graph* g, const uint8_t* part, unsigned long long* fp,
+                                   unsigned long long* ms, int* bad, int64_t* fin, cudaStream_t s) {
+  const int G = makespan_group(g->n, g->m);
+  const int32_t nlev = g->nlev;
+  switch (G) {
+#define GP_MS(GG)                                                                                      \
+  case GG: {                                                                                           \
+    const int cmax = cluster_max((const void*)k_makespan<GG>, 1024);                                   \
+    if (cmax <= 0) return cudaErrorLaunchFailure;                                                      \
+    int64_t want = (g->max_width * GG + 1023) / 1024;                                                  \
+    const int cs = (int)(want < 1 ? 1 : (want < cmax ? want : cmax));                                  \
+    return launch_cluster(F_MAKESPAN, k_makespan<GG>, cs, 1024, s, nlev, (const int64_t*)g->lev_ptr,    \
+                          (const int32_t*)g->lev_vtx, (const int64_t*)g->lo_off, (const int32_t*)g->lo_src, \
+                          (const int32_t*)g->lo_w, (const int32_t*)g->lo_cC, (const int32_t*)g->lo_cG, part, \
+                          fp, ms, bad, fin);                                                           \
+  }
+    GP_MS(2) GP_MS(4) GP_MS(8) GP_MS(16) GP_MS(32)
+#undef GP_MS
+  }
+  return cudaErrorInvalidValue;
 }
 
 extern "C" {
@@ -372,40 +415,42 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     if (n) GP_LAUNCH(F_TRANSPOSE, k_fill_in, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off,
                      indeg, in_src, in_w, flags);
     GP_CHECK_LAUNCH();
-    // ---- topological levels (cooperative, grid barrier per level)
+    // ---- topological levels (one thread-block cluster, hardware cluster barrier per level)
     g->lev_vtx = g->own<int32_t>(n, s);
     g->lev_ptr = g->own<int64_t>(n + 2, s);
     g->level = g->own<int32_t>(n, s);
     int32_t* rem = A.get<int32_t>(n);
-    unsigned long long* tail = A.get<unsigned long long>(2);
+    unsigned long long* tail = A.get<unsigned long long>(4);  // 3 rotating level counters + total
     int32_t* nlev_dev = A.get<int32_t>(1);
-    unsigned* bar = A.get<unsigned>(2);
-    int* err = A.get<int>(1);
-    GP_CUDA(cudaMemsetAsync(tail, 0, 2 * sizeof(unsigned long long), s));
+    GP_CUDA(cudaMemsetAsync(tail, 0, 4 * sizeof(unsigned long long), s));
     GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), s));
-    GP_CUDA(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
-    GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     if (n) {
-      const int bps = coop_blocks_per_sm((const void*)k_levels, 256, 0);
-      int grid = num_sms() * (bps < 2 ? bps : 2);
-      const int64_t need = (n + 255) / 256;
-      if (need < grid) grid = (int)need;
       int64_t nn = n;
-      int64_t* off_p = g->off;
-      int32_t* cols_p = g->cols;
-      void* args[] = {&nn, &off_p, &cols_p, &in_off, &rem, &g->lev_vtx, &g->lev_ptr, &g->level, &tail, &nlev_dev, &bar, &err};
-      GP_CUDA(launch_coop(F_LEVELS, (const void*)k_levels, grid, 256, 0, s, args));
+      const int G = makespan_group(n, m);
+      int ok = 0;
+      switch (G) {
+#define GP_LEV(GG)                                                                                       \
+  case GG: {                                                                                            \
+    const int cs = cluster_max((const void*)k_levels<GG>, 1024);                                        \
+    if (cs > 0) {                                                                                       \
+      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, s, nn, (const int64_t*)g->off,            \
+                             (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->lev_ptr, \
+                             g->level, tail, nlev_dev));                                                \
+      ok = 1;                                                                                           \
+    }                                                                                                   \
+  } break;
+        GP_LEV(2) GP_LEV(4) GP_LEV(8) GP_LEV(16) GP_LEV(32)
+#undef GP_LEV
+      }
+      if (!ok) throw Fail{GP_ERR_CUDA};
     }
     unsigned long long htail = 0;
-    int herr = 0;
     int32_t hnlev = 0;
     GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(&htail, tail, sizeof(htail), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&htail, tail + 3, sizeof(htail), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaMemcpyAsync(&hnlev, nlev_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
-    if (herr) throw Fail{(gp_status)herr};
-    if ((hflags & VF_SELFLOOP) || (int64_t)htail != n) throw Fail{GP_ERR_NOT_DAG};
+    if ((hflags & VF_SELFLOOP) || (n > 0 && (int64_t)htail != n)) throw Fail{GP_ERR_NOT_DAG};
     g->nlev = hnlev;
     {
       std::vector<int64_t> lp((size_t)hnlev + 1);
@@ -722,35 +767,15 @@ gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan,
     struct Small {
       unsigned long long ms;
       int bad;
-      int err;
-      unsigned bar[2];
+      int pad;
     };
     Small* sm = A.get<Small>(1);
     GP_CUDA(cudaMemsetAsync(sm, 0, sizeof(Small), s));
-    const int G = makespan_group(n, g->m);
-    const void* fn = G == 2 ? (const void*)k_makespan<2>
-                     : G == 4 ? (const void*)k_makespan<4>
-                     : G == 8 ? (const void*)k_makespan<8>
-                     : G == 16 ? (const void*)k_makespan<16> : (const void*)k_makespan<32>;
-    const int bps = coop_blocks_per_sm(fn, 256, 0);
-    const int64_t cap = (int64_t)num_sms() * bps;
-    int64_t want = (g->max_width * G + 255) / 256;
-    if (want < 1) want = 1;
-    const int grid = (int)(want < cap ? want : cap);
-    int32_t nlev = g->nlev;
-    unsigned long long* msp = &sm->ms;
-    int* badp = &sm->bad;
-    int* errp = &sm->err;
-    unsigned* barp = sm->bar;
-    void* args[] = {&nlev, (void*)&g->lev_ptr, (void*)&g->lev_vtx, (void*)&g->lo_off, (void*)&g->lo_src,
-                    (void*)&g->lo_w, (void*)&g->lo_cC, (void*)&g->lo_cG, (void*)&p, &fp, &msp, &badp, &fin,
-                    &barp, &errp};
-    GP_CUDA(launch_coop(F_MAKESPAN, fn, grid, 256, 0, s, args));
+    GP_CUDA(launch_makespan(g, p, fp, &sm->ms, &sm->bad, fin, s));
     Small h;
     GP_CUDA(cudaMemcpyAsync(&h, sm, sizeof(Small), cudaMemcpyDeviceToHost, s));
     if (fin_host) GP_CUDA(cudaMemcpyAsync(finish_out, fin, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
-    if (h.err) return (gp_status)h.err;
     if (h.bad) return GP_ERR_INVALID;
     *makespan = (int64_t)h.ms;
     return GP_OK;

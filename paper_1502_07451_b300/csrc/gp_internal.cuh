@@ -51,9 +51,6 @@ bool prof_on();
     ::gp::launch_end((fam), (stream));                                        \
   } while (0)
 
-// cooperative launch helper; returns cudaError_t
-cudaError_t launch_coop(int family, const void* fn, int grid, int block, size_t smem, cudaStream_t s,
-                        void** args);
 
 // ------------------------------------------------------------------------------------------------
 // Error helpers.
@@ -169,62 +166,37 @@ __device__ __forceinline__ void account(int fam, unsigned long long bytes_this_t
 }
 
 // ------------------------------------------------------------------------------------------------
-// Grid barrier for cooperative persistent kernels.  Bounded spin: after kSpinLimit polls the
-// waiting block records GP_ERR_TIMEOUT in *err and every block leaves its loop.
-// bar[0] = arrival counter, bar[1] = generation.
+// Thread-block clusters.  Level-synchronous loops (topological levels, makespan) run in ONE cluster
+// of up to 16 CTAs x 1024 threads and separate levels with the hardware cluster barrier; data that
+// other CTAs wrote before the barrier is read with L2-only loads (__ldcg).
 // ------------------------------------------------------------------------------------------------
-constexpr long long kSpinLimit = 1ll << 26;
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ int ld_acquire_i32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;\n" ::: "memory");
 }
 
-// Returns false if the barrier timed out (or an earlier barrier did): callers must then return.
-// If snap_src is given, the last block to arrive copies *snap_src to *snap_dst before releasing the
-// others: a value that every block wrote to before arriving is then read consistently afterwards,
-// even while fast blocks already modify *snap_src again.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err,
-                                             const unsigned long long* snap_src = nullptr,
-                                             unsigned long long* snap_dst = nullptr) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = ld_acquire_i32(err) == 0;
-    if (ok) {
-      const unsigned gen = ld_acquire_u32(bar + 1);
-      __threadfence();
-      const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-      if (arrived == gridDim.x) {
-        if (snap_src) *(volatile unsigned long long*)snap_dst = atomicAdd((unsigned long long*)snap_src, 0ull);
-        atomicExch(bar, 0u);
-        __threadfence();
-        st_release_u32(bar + 1, gen + 1u);
-      } else {
-        long long spins = 0;
-        while (ld_acquire_u32(bar + 1) == gen) {
-          if (++spins > kSpinLimit || ld_acquire_i32(err) != 0) {
-            atomicCAS(err, 0, (int)GP_ERR_TIMEOUT);
-            ok = 0;
-            break;
-          }
-          __nanosleep(64);
-        }
-      }
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
+// Largest cluster (16 if the device allows non-portable sizes, else 8) that can be resident for
+// `fn` with `block` threads per CTA; 0 if none.
+int cluster_max(const void* fn, int block);
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_cluster(int family, void (*kern)(KArgs...), int csize, int block, cudaStream_t s,
+                           Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)csize);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)csize;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  launch_begin(family, s);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+  launch_end(family, s);
+  return e;
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -16,7 +16,7 @@
 
 namespace gp {
 
-// words [0, 8): control (result, flags, grid barrier); words [8, 8 + max n): finish times
+// words [0, 8): control (result, flags); words [8, 8 + max n): finish times
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[8 + GP_MAKESPAN_NOALLOC_MAX_N];
 
 static std::mutex g_noalloc_mu;
@@ -61,40 +61,22 @@ extern "C" gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part,
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* msp = base;                  // word 0: makespan
   int* badp = (int*)(base + 1);                    // word 1: a part value > 1 was seen
-  int* errp = (int*)(base + 2);                    // word 2: barrier timeout
-  unsigned* barp = (unsigned*)(base + 3);          // word 3: barrier counter and generation
   unsigned long long* fp = base + 8;               // finish times, written before they are read
   // the control words must start at zero; the finish area needs no clearing
   if (cudaMemsetAsync(base, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
-  const int G = makespan_group(n, g->m);
-  const void* fn = G == 2 ? (const void*)k_makespan<2>
-                   : G == 4 ? (const void*)k_makespan<4>
-                   : G == 8 ? (const void*)k_makespan<8>
-                   : G == 16 ? (const void*)k_makespan<16> : (const void*)k_makespan<32>;
-  const int bps = coop_blocks_per_sm(fn, 256, 0);
-  const int64_t cap = (int64_t)num_sms() * bps;
-  int64_t want = (g->max_width * G + 255) / 256;
-  if (want < 1) want = 1;
-  const int grid = (int)(want < cap ? want : cap);
-  int32_t nlev = g->nlev;
-  int64_t* fin = finish_out;
-  void* args[] = {&nlev, (void*)&g->lev_ptr, (void*)&g->lev_vtx, (void*)&g->lo_off, (void*)&g->lo_src,
-                  (void*)&g->lo_w, (void*)&g->lo_cC, (void*)&g->lo_cG, (void*)&part, &fp, &msp, &badp, &fin,
-                  &barp, &errp};
-  if (launch_coop(F_MAKESPAN, fn, grid, 256, 0, s, args) != cudaSuccess) {
+  if (launch_makespan(g, part, fp, msp, badp, finish_out, s) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
-  unsigned long long ctl[3];
+  unsigned long long ctl[2];
   if (cudaMemcpyAsync(ctl, base, sizeof(ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
-  if ((int)ctl[2]) return (gp_status)(int)ctl[2];
   if ((int)ctl[1]) return GP_ERR_INVALID;
   *makespan = (int64_t)ctl[0];
   return GP_OK;

@@ -73,51 +73,60 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Kahn's algorithm, level-synchronous, in one cooperative launch.  Level l holds the vertices whose
-// longest path from a source has l edges: lev_vtx[lev_ptr[l] .. lev_ptr[l+1]).
-__global__ void __launch_bounds__(256)
+// Kahn's algorithm, level-synchronous, in one thread-block cluster.  Level l holds the vertices
+// whose longest path from a source has l edges: lev_vtx[lev_ptr[l] .. lev_ptr[l+1]).  A group of G
+// lanes expands one frontier vertex.  New frontier vertices of level l+1 are appended after the
+// current level with counter cnt[(l+1) % 3]; the counter of level l+2 is cleared during level l, after
+// every thread has read it as the size of level l-1, so one barrier per level suffices.
+// cnt[3] receives the number of vertices placed (n exactly when the graph is acyclic).
+template <int G>
+__global__ void __launch_bounds__(1024)
     k_levels(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
              const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int64_t* lev_ptr,
-             int32_t* level, unsigned long long* tail, int32_t* nlev_out, unsigned* bar, int* err) {
-  // tail: next free slot of lev_vtx (appends); tail + 1: its value when the last barrier released
-  const int lane = threadIdx.x & 31;
+             int32_t* level, unsigned long long* cnt, int32_t* nlev_out) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t gw = tid >> 5, nw = stride >> 5;
+  const int64_t group = tid / G, ngroups = stride / G;
+  const int sub = (int)(tid % G);
   for (int64_t v = tid; v < n; v += stride) {
     const int32_t d = (int32_t)(in_off[v + 1] - in_off[v]);
     rem[v] = d;
     if (d == 0) {
-      const unsigned long long pos = atomicAdd(tail, 1ull);
+      const unsigned long long pos = atomicAdd(&cnt[0], 1ull);
       lev_vtx[pos] = (int32_t)v;
       level[v] = 0;
     }
   }
-  if (!grid_barrier(bar, err, tail, tail + 1)) return;
-  int64_t beg = 0, end = (int64_t) * (volatile unsigned long long*)(tail + 1);
+  cluster_sync();
+  int64_t beg = 0, end = (int64_t) * (volatile unsigned long long*)&cnt[0];
   int32_t lev = 0;
   while (end > beg) {
-    if (tid == 0) lev_ptr[lev] = beg;
-    for (int64_t i = beg + gw; i < end; i += nw) {
-      const int32_t v = __ldcg(lev_vtx + i);  // written by other blocks: bypass L1
+    if (tid == 0) {
+      lev_ptr[lev] = beg;
+      cnt[(lev + 2) % 3] = 0;
+    }
+    unsigned long long* app = &cnt[(lev + 1) % 3];
+    for (int64_t i = beg + group; i < end; i += ngroups) {
+      const int32_t v = __ldcg(lev_vtx + i);  // written by other CTAs: bypass L1
       const int64_t eb = off[v], ee = off[v + 1];
-      for (int64_t e = eb + lane; e < ee; e += 32) {
+      for (int64_t e = eb + sub; e < ee; e += G) {
         const int32_t u = cols[e];
         if (atomicSub(&rem[u], 1) == 1) {
-          const unsigned long long pos = atomicAdd(tail, 1ull);
-          lev_vtx[pos] = u;
+          const unsigned long long k = atomicAdd(app, 1ull);
+          lev_vtx[end + (int64_t)k] = u;
           level[u] = lev + 1;
         }
       }
     }
-    if (!grid_barrier(bar, err, tail, tail + 1)) return;
+    cluster_sync();
     beg = end;
-    end = (int64_t) * (volatile unsigned long long*)(tail + 1);
+    end = beg + (int64_t) * (volatile unsigned long long*)app;
     lev++;
   }
   if (tid == 0) {
     lev_ptr[lev] = beg;
     *nlev_out = lev;
+    cnt[3] = (unsigned long long)beg;
   }
 }
 

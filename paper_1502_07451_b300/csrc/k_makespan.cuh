@@ -2,8 +2,8 @@
 //
 // finish(v) = t_side(v)(v) + max over entries u->v of (finish(u) + [side(u) != side(v)] w(u,v)),
 // the max over no entries being 0, and makespan = max_v finish(v).  Vertices are visited level by
-// level of the topological order (one cooperative launch, a grid barrier between levels); within a
-// level, a group of G lanes reduces one vertex's in-entries.  finish is kept by level position,
+// level of the topological order (one thread-block cluster, the hardware cluster barrier between
+// levels); within a level, a group of G lanes reduces one vertex's in-entries.  finish is kept by level position,
 // packed with the side bit (2 finish + side) so one gather gives both.
 #pragma once
 #include "gp_internal.cuh"
@@ -11,13 +11,13 @@
 namespace gp {
 
 template <int G>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(1024)
     k_makespan(int32_t nlev, const int64_t* __restrict__ lev_ptr, const int32_t* __restrict__ lev_vtx,
                const int64_t* __restrict__ lo_off, const int32_t* __restrict__ lo_src,
                const int32_t* __restrict__ lo_w, const int32_t* __restrict__ lo_cC,
                const int32_t* __restrict__ lo_cG, const uint8_t* __restrict__ part,
                unsigned long long* fp, unsigned long long* ms_out, int* bad_part,
-               int64_t* __restrict__ finish_out, unsigned* bar, int* err) {
+               int64_t* __restrict__ finish_out) {
   __shared__ unsigned long long sh[32];
   __shared__ unsigned long long sacc[32];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256)
         if (finish_out) finish_out[lev_vtx[i]] = (int64_t)fin;
       }
     }
-    if (!grid_barrier(bar, err)) return;
+    cluster_sync();
   }
   // block max
   {
