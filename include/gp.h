@@ -192,7 +192,8 @@ GP_API gp_status gp_step_match(int64_t n, const int64_t* off, const int32_t* adj
 /* Contraction of a matching: representatives (unmatched, or the smaller of a pair) are numbered in
  * vertex order; cmap_out int32[n]; coarse graph written in compact CSR to coff int64[n+1] (first
  * nc+1 used), cadj int32[a], cW int64[a], cvC / cvG int64[n] (first nc used); *nc_out, *ac_out
- * receive the coarse sizes (host). */
+ * receive the coarse sizes (host).  Entries within a coarse row are in no particular order (every
+ * later step is independent of it). */
 GP_API gp_status gp_step_contract(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
                            const int64_t* vC, const int64_t* vG, const int32_t* mate, int32_t* cmap_out,
                            int64_t* coff, int32_t* cadj, int64_t* cW, int64_t* cvC, int64_t* cvG,

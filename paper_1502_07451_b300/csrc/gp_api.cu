@@ -660,12 +660,17 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     cand.gain = A.get<long long>(n);
     cand.cd = A.get<long long>(n);
     cand.cs = A.get<long long>(n);
+    cand.gainv = A.get<long long>(n);
+    cand.stamp = A.get<int32_t>(n);
+    cand.dirty[0] = A.get<int32_t>(n);
+    cand.dirty[1] = A.get<int32_t>(n);
+    GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
     for (int l = Lc; l >= 0; l--) {
       if (l < Lc) {
         parts[l] = A.get<uint8_t>(L[l].n);
         project(L[l].n, cmaps[l], parts[l + 1], parts[l], s);
       }
-      refine_level_run(L[l], parts[l], &td->ctl, cand, s);
+      refine_level_run(L[l], parts[l], &td->ctl, cand, l, (double)T.a[l] / (double)(T.n[l] > 0 ? T.n[l] : 1), s);
       GP_LAUNCH(F_MISC, k_ref_end, 1, 1, 0, s, &td->ctl, l, td->rounds, td->moves, td->bal, td->balmoves);
     }
     if (prof) cudaEventRecord(ev[3], s);
@@ -792,6 +797,10 @@ static LevelGraph view_of(int64_t n, const int64_t* off, const int32_t* adj, con
                           const int64_t* vG, Arena& A, cudaStream_t s) {
   LevelGraph L;
   L.n = n;
+  int64_t a = 0;
+  GP_CUDA(cudaMemcpyAsync(&a, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GP_CUDA(cudaStreamSynchronize(s));
+  L.cap = a;
   L.start = const_cast<int64_t*>(off);
   L.deg = A.get<int32_t>(n);
   L.adj = const_cast<int32_t*>(adj);
@@ -936,9 +945,17 @@ gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, cons
     cand.gain = A.get<long long>(n);
     cand.cd = A.get<long long>(n);
     cand.cs = A.get<long long>(n);
+    cand.gainv = A.get<long long>(n);
+    cand.stamp = A.get<int32_t>(n);
+    cand.dirty[0] = A.get<int32_t>(n);
+    cand.dirty[1] = A.get<int32_t>(n);
     if (n) {
+      int64_t a = 0;
+      GP_CUDA(cudaMemcpyAsync(&a, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
+      GP_CUDA(cudaStreamSynchronize(s));
       refine_loads(L, part, ctl, s);
-      refine_level_run(L, part, ctl, cand, s);
+      refine_level_run(L, part, ctl, cand, 0, (double)a / (double)n, s);
     }
     GP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));

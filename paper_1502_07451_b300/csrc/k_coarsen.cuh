@@ -115,78 +115,222 @@ __global__ void __launch_bounds__(256)
   account(F_TWOHOP, bytes, sacc);
 }
 
-// Pairs the vertices anchored at h in ascending neighbour order.  Sequentially: a vertex joins the
+// Pairs the vertices anchored at h in ascending vertex order.  Sequentially: a vertex joins the
 // pending one when the caps allow (pair formed, nothing pending), else it becomes pending.  With
 // P_i = "item i is pending after its turn" and ok_i = "caps allow item i-1 with item i":
 // P_i = !(P_{i-1} && ok_i), so P flips along runs of ok and resets to true where ok fails; item i is
-// paired with item i-1 exactly when P_i is false.  A warp evaluates this 32 row entries at a time
-// with a max-scan of the last reset position, carrying the last item across chunks.
-__global__ void __launch_bounds__(256)
-    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
-             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate) {
-  __shared__ unsigned long long sacc[32];
+// paired with item i-1 exactly when P_i is false.  A warp evaluates this 32 items at a time with a
+// max-scan of the last reset position, carrying the last item across chunks.
+// `items` holds the anchored vertices sorted ascending; `nitems` of them.
+__device__ void pair_sorted(const LevelGraph& g, int64_t capC, int64_t capG, const int32_t* items, int64_t nitems,
+                            int32_t* __restrict__ mate, unsigned long long& bytes) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t p_id = -1;  // carried last item
+  int64_t p_c = 0, p_g = 0;
+  bool p_pend = false;
+  for (int64_t base = 0; base < nitems; base += 32) {
+    const bool flag = base + lane < nitems;
+    const int32_t v = flag ? items[base + lane] : -1;
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    int64_t vc = 0, vg = 0;
+    if (flag) {
+      vc = g.vC[v];
+      vg = g.vG[v];
+      bytes += 20;
+    }
+    const unsigned below = m & lt;
+    const int pred_lane = below ? 31 - __clz(below) : -1;
+    const int srcl = pred_lane >= 0 ? pred_lane : lane;
+    int32_t q_id = __shfl_sync(0xffffffffu, v, srcl);
+    int64_t q_c = __shfl_sync(0xffffffffu, vc, srcl);
+    int64_t q_g = __shfl_sync(0xffffffffu, vg, srcl);
+    if (pred_lane < 0) {
+      q_id = p_id;
+      q_c = p_c;
+      q_g = p_g;
+    }
+    const bool okprev = flag && q_id >= 0 && (q_c + vc <= capC) && (q_g + vg <= capG);
+    const int sidx = __popc(below);
+    int scan = (flag && !okprev) ? sidx : INT_MIN;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, scan, o);
+      if (lane >= o) scan = y > scan ? y : scan;
+    }
+    const int r0 = (p_id >= 0 && p_pend) ? -1 : -2;
+    const int lr = scan > r0 ? scan : r0;
+    const bool P = ((sidx - lr) & 1) == 0;
+    if (flag && !P) {
+      mate[v] = q_id;
+      mate[q_id] = v;
+      bytes += 8;
+    }
+    const int last = 31 - __clz(m);
+    p_id = __shfl_sync(0xffffffffu, v, last);
+    p_c = __shfl_sync(0xffffffffu, vc, last);
+    p_g = __shfl_sync(0xffffffffu, vg, last);
+    p_pend = __shfl_sync(0xffffffffu, P, last);
+  }
+}
+
+__device__ __forceinline__ void warp_bitonic_keys(int32_t* K, int P, int lane) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const int32_t a = K[i], b = K[ixj];
+          if ((a > b) == ((i & k) == 0)) {
+            K[i] = b;
+            K[ixj] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+constexpr int kSatCap = 1024;  // anchored vertices a warp sorts in shared memory
+constexpr int kTwohopWarps = 8;
+
+// Warp per anchor: gathers its anchored vertices (rows are in no particular order), sorts them and
+// pairs them.  Anchors with more than kSatCap of them go to a list for k_twohop_big.
+__global__ void __launch_bounds__(kTwohopWarps * 32)
+    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
+             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate, int32_t* __restrict__ big,
+             unsigned* big_cnt) {
+  __shared__ int32_t sat[kTwohopWarps][kSatCap];
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = lanemask_lt();
+  int32_t* S = sat[wib];
+  const int64_t gw = (int64_t)blockIdx.x * kTwohopWarps + wib;
+  const int64_t nw = (int64_t)gridDim.x * kTwohopWarps;
   unsigned long long bytes = 0;
   for (int64_t h = gw; h < g.n; h += nw) {
     if (!is_anchor[h]) continue;
     const int64_t b = g.start[h];
     const int32_t d = g.deg[h];
-    int32_t p_id = -1;  // carried last item (any earlier chunk)
-    int64_t p_c = 0, p_g = 0;
-    bool p_pend = false;
-    for (int32_t base = 0; base < d; base += 32) {
-      const int32_t k = base + lane;
+    int k = 0;
+    bool over = false;
+    for (int32_t base = 0; base < d && !over; base += 32) {
+      const int32_t q = base + lane;
       int32_t v = -1;
       bool flag = false;
-      if (k < d) {
-        v = g.adj[b + k];
+      if (q < d) {
+        v = g.adj[b + q];
         flag = anchor[v] == (int32_t)h;
         bytes += 8;
       }
       const unsigned m = __ballot_sync(0xffffffffu, flag);
-      if (m == 0) continue;
-      int64_t vc = 0, vg = 0;
-      if (flag) {
-        vc = g.vC[v];
-        vg = g.vG[v];
-        bytes += 16;
+      if (k + __popc(m) > kSatCap) {
+        over = true;
+        break;
       }
-      const unsigned below = m & lt;
-      const int pred_lane = below ? 31 - __clz(below) : -1;
-      const int srcl = pred_lane >= 0 ? pred_lane : lane;
-      int32_t q_id = __shfl_sync(0xffffffffu, v, srcl);
-      int64_t q_c = __shfl_sync(0xffffffffu, vc, srcl);
-      int64_t q_g = __shfl_sync(0xffffffffu, vg, srcl);
-      if (pred_lane < 0) {
-        q_id = p_id;
-        q_c = p_c;
-        q_g = p_g;
-      }
-      const bool okprev = flag && q_id >= 0 && (q_c + vc <= capC) && (q_g + vg <= capG);
-      const int sidx = __popc(below);
-      int scan = (flag && !okprev) ? sidx : INT_MIN;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, scan, o);
-        if (lane >= o) scan = y > scan ? y : scan;
-      }
-      const int r0 = (p_id >= 0 && p_pend) ? -1 : -2;
-      const int lr = scan > r0 ? scan : r0;
-      const bool P = ((sidx - lr) & 1) == 0;
-      if (flag && !P) {
-        mate[v] = q_id;
-        mate[q_id] = v;
-        bytes += 8;
-      }
-      const int last = 31 - __clz(m);
-      p_id = __shfl_sync(0xffffffffu, v, last);
-      p_c = __shfl_sync(0xffffffffu, vc, last);
-      p_g = __shfl_sync(0xffffffffu, vg, last);
-      p_pend = __shfl_sync(0xffffffffu, P, last);
+      if (flag) S[k + __popc(m & lt)] = v;
+      k += __popc(m);
     }
+    if (over) {
+      if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
+      continue;
+    }
+    if (k == 0) continue;
+    int P = 32;
+    while (P < k) P <<= 1;
+    for (int i = k + lane; i < P; i += 32) S[i] = INT32_MAX;
+    __syncwarp();
+    warp_bitonic_keys(S, P, lane);
+    pair_sorted(g, capC, capG, S, k, mate, bytes);
+    __syncwarp();
+  }
+  account(F_TWOHOP, bytes, sacc);
+}
+
+// Block per anchor with more than kSatCap anchored vertices: gather them into scratch (the anchor's
+// row region), LSD radix sort by vertex id (8-bit digits), then one warp pairs them.
+__global__ void __launch_bounds__(1024)
+    k_twohop_big(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
+                 int32_t* __restrict__ mate, const int32_t* __restrict__ big, const unsigned* big_cnt,
+                 int32_t* __restrict__ ta, int32_t* __restrict__ tb, int nbits) {
+  __shared__ unsigned s_k;
+  __shared__ unsigned hist[256];
+  __shared__ unsigned binbase[256];
+  __shared__ int wcnt[32][256];
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned lt = lanemask_lt();
+  unsigned long long bytes = 0;
+  const unsigned nbig = *big_cnt;
+  for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const int32_t h = big[bi];
+    const int64_t b = g.start[h];
+    const int32_t d = g.deg[h];
+    if (threadIdx.x == 0) s_k = 0;
+    __syncthreads();
+    for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {
+      const int32_t v = g.adj[b + q];
+      if (anchor[v] == h) ta[b + atomicAdd(&s_k, 1u)] = v;
+    }
+    __syncthreads();
+    const int64_t N = s_k;
+    int32_t* src = ta + b;
+    int32_t* dst = tb + b;
+    for (int shift = 0; shift < nbits; shift += 8) {
+      for (int x = threadIdx.x; x < 256; x += blockDim.x) hist[x] = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[(src[i] >> shift) & 255], 1u);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int x = 0; x < 256; x++) {
+          binbase[x] = run;
+          run += hist[x];
+        }
+      }
+      __syncthreads();
+      for (int64_t tile = 0; tile < N; tile += blockDim.x) {
+        const int64_t i = tile + threadIdx.x;
+        const bool valid = i < N;
+        for (int x = lane; x < 256; x += 32) wcnt[wid][x] = 0;
+        __syncwarp();
+        int32_t key = 0;
+        int dg = 0, rank = 0;
+        if (valid) {
+          key = src[i];
+          dg = (key >> shift) & 255;
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+          const unsigned peers = __match_any_sync(act, dg);
+          rank = __popc(peers & lt);
+          if (rank == 0) wcnt[wid][dg] = __popc(peers);
+        }
+        __syncthreads();
+        unsigned tilecnt = 0;
+        if (threadIdx.x < 256) {
+          int run = 0;
+          for (int w = 0; w < nwarps; w++) {
+            const int c = wcnt[w][threadIdx.x];
+            wcnt[w][threadIdx.x] = run;
+            run += c;
+          }
+          tilecnt = (unsigned)run;
+        }
+        __syncthreads();
+        if (valid) dst[binbase[dg] + wcnt[wid][dg] + rank] = key;
+        __syncthreads();
+        if (threadIdx.x < 256) binbase[threadIdx.x] += tilecnt;
+        __syncthreads();
+      }
+      int32_t* t = src;
+      src = dst;
+      dst = t;
+    }
+    if (wid == 0) pair_sorted(g, capC, capG, src, N, mate, bytes);
+    if (threadIdx.x == 0) bytes += 12ull * (unsigned long long)d;
+    __syncthreads();
   }
   account(F_TWOHOP, bytes, sacc);
 }
@@ -239,9 +383,23 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
   if (twohop) {
     int32_t* anchor = pick;  // reuse
     uint8_t* is_anchor = alive;
+    unsigned* big_cnt = dnew<unsigned>(1, s);
+    int32_t* big = dnew<int32_t>(n, s);
+    int32_t* ta = dnew<int32_t>(g.cap, s);
+    int32_t* tb = dnew<int32_t>(g.cap, s);
     GP_CUDA(cudaMemsetAsync(is_anchor, 0, (size_t)n, s));
+    GP_CUDA(cudaMemsetAsync(big_cnt, 0, sizeof(unsigned), s));
     GP_LAUNCH(F_TWOHOP, k_anchor, grid_for(n * 32, 256), 256, 0, s, g, seed, mate, anchor, is_anchor);
-    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n * 32, 256), 256, 0, s, g, capC, capG, anchor, is_anchor, mate);
+    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n, kTwohopWarps, 16), kTwohopWarps * 32, 0, s, g, capC, capG, anchor,
+              is_anchor, mate, big, big_cnt);
+    int nbits = 1;
+    while (nbits < 31 && (int64_t(1) << nbits) < n) nbits++;
+    GP_LAUNCH(F_TWOHOP, k_twohop_big, (unsigned)num_sms(), 1024, 0, s, g, capC, capG, anchor, mate, big, big_cnt,
+              ta, tb, nbits);
+    dfree(big_cnt, s);
+    dfree(big, s);
+    dfree(ta, s);
+    dfree(tb, s);
   }
   GP_CHECK_LAUNCH();
   dfree(pick, s);
@@ -285,7 +443,7 @@ void contract_level(const LevelGraph& g, const int32_t* mate, int32_t* cmap, Lev
   src.row_b = mate_of;
   src.map = cmap;
   src.drop_self = 1;
-  merge_rows(src, nc, nc, cg.start, cg.deg, cg.adj, cg.W, F_CONTRACT_MERGE, cg.cap, s);
+  merge_rows_unordered(src, nc, nc, cg.start, cg.deg, cg.adj, cg.W, F_CONTRACT_MERGE, cg.cap, s);
   dfree(rep_of, s);
   dfree(mate_of, s);
   dfree(rawlen, s);

@@ -38,6 +38,7 @@ struct Ctl {
   int32_t idbits, side_src;
   int32_t done, streak, rounds, balanced, bal_active, pad;
   long long moves, bal_moves, take;
+  unsigned long long ndirty[2];  // vertices whose gain a round's moves changed, double-buffered
 };
 
 struct Cands {
@@ -45,7 +46,13 @@ struct Cands {
   long long* gain;
   long long* cd;  // weight joining the destination
   long long* cs;  // weight leaving the source
+  long long* gainv;   // current gain of every vertex of the level
+  int32_t* stamp;     // round tag of the last round whose moves made the vertex's gain stale
+  int32_t* dirty[2];  // the vertices stamped by a round, double-buffered by round parity
 };
+
+// tag of round r (-1 = balance) at level l; stamps start at -1
+__host__ __device__ __forceinline__ int32_t round_tag(int level, int r) { return (level << 4) | (r + 2); }
 
 __device__ __forceinline__ u128 cand_key(long long gmax, long long gain, int32_t id, int idbits) {
   return ((u128)(unsigned long long)(gmax - gain) << idbits) | (u128)(uint32_t)id;
@@ -86,6 +93,8 @@ __global__ void k_ref_begin(Ctl* ctl, int idbits) {
   c.bal_moves = 0;
   c.sel_round = -2;
   c.idbits = idbits;
+  c.ndirty[0] = 0;
+  c.ndirty[1] = 0;
   reset_counters(c.cc[0]);
   reset_counters(c.cc[1]);
   const bool overC = c.LC > c.BC, overG = c.LG > c.BG;
@@ -99,70 +108,111 @@ __global__ void k_ref_begin(Ctl* ctl, int idbits) {
   }
 }
 
-// r = -1: balance round, else gain round r.  Warp per 32 consecutive vertices.
+// gain of every vertex (a group of G lanes per row), once per level
+template <int G>
 __global__ void __launch_bounds__(256)
-    k_ref_gain(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, Cands cand) {
+    k_gain_all(LevelGraph g, const uint8_t* __restrict__ part, long long* __restrict__ gainv) {
+  __shared__ unsigned long long sacc[32];
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int sub = threadIdx.x % G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  unsigned long long bytes = 0;
+  const int64_t nfull = (g.n + ngroups - 1) / ngroups * ngroups;  // every group runs the same trips
+  for (int64_t v = group; v < nfull; v += ngroups) {
+    long long acc = 0;
+    if (v < g.n) {
+      const uint8_t p = part[v];
+      const int64_t b = g.start[v];
+      const int32_t d = g.deg[v];
+      for (int32_t k = sub; k < d; k += G) {
+        const long long w = g.W[b + k];
+        acc += (part[g.adj[b + k]] == p) ? -w : w;
+      }
+      if (sub == 0) bytes += 21ull + 13ull * (unsigned long long)d;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
+    if (v < g.n && sub == 0) gainv[v] = acc;
+  }
+  account(F_GAIN, bytes, sacc);
+}
+
+__device__ __forceinline__ void push_cand(CandCounters* cc, const Cands& cand, int32_t v, long long gain,
+                                          long long cdv, long long csv, unsigned long long& sum_cd,
+                                          unsigned long long& sum_cs, long long& gmax, long long& gmin) {
+  const unsigned long long slot = atomicAdd(&cc->ncand, 1ull);
+  cand.id[slot] = v;
+  cand.gain[slot] = gain;
+  cand.cd[slot] = cdv;
+  cand.cs[slot] = csv;
+  sum_cd += (unsigned long long)cdv;
+  sum_cs += (unsigned long long)csv;
+  gmax = gain > gmax ? gain : gmax;
+  gmin = gain < gmin ? gain : gmin;
+}
+
+// Candidates of round r (-1 = balance): from the stored gains, except for the vertices the previous
+// round's moves made stale (stamp == prev_tag), whose gains are recomputed here by a warp each and
+// stored back.  Both parts write disjoint vertices.
+__global__ void __launch_bounds__(256)
+    k_ref_cands(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag, Cands cand) {
   __shared__ long long sh[32];
   __shared__ unsigned long long shu[32];
   __shared__ unsigned long long sacc[32];
   __shared__ int s_src, s_skip;
+  __shared__ unsigned long long s_nd;
   if (threadIdx.x == 0) {
     s_skip = (r < 0) ? !ctl->bal_active : ctl->done;
     s_src = (r < 0) ? ctl->side_src : (r & 1);
+    s_nd = (r < 0) ? 0ull : ctl->ndirty[r & 1];
   }
   __syncthreads();
   if (s_skip) return;
   const int src = s_src;
   const int par = (r < 0) ? 1 : (r & 1);
   CandCounters* cc = &ctl->cc[par];
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t* cdst = src == 0 ? g.vG : g.vC;
   const int64_t* csrc = src == 0 ? g.vC : g.vG;
   unsigned long long sum_cd = 0, sum_cs = 0, bytes = 0;
   long long gmax = LLONG_MIN, gmin = LLONG_MAX;
-  for (int64_t base = gw * 32; base < g.n; base += nw * 32) {
-    const int64_t mv = base + lane;
-    const bool on = mv < g.n && part[mv] == src;
-    unsigned m = __ballot_sync(0xffffffffu, on);
-    if (lane == 0) bytes += 32;
-    while (m) {
-      const int bit = __ffs(m) - 1;
-      m &= m - 1;
-      const int64_t v = base + bit;
-      const int64_t b = g.start[v];
-      const int32_t d = g.deg[v];
-      long long ext = 0, in = 0;
-      for (int32_t k = lane; k < d; k += 32) {
-        const int64_t w = g.W[b + k];
-        if (part[g.adj[b + k]] == src)
-          in += w;
-        else
-          ext += w;
-      }
-      const long long gain = warp_sum64(ext) - warp_sum64(in);
-      if (lane == 0) {
-        bytes += 12ull + 13ull * (unsigned long long)d;
-        if (r < 0 || gain > 0) {
-          const unsigned long long slot = atomicAdd(&cc->ncand, 1ull);
-          const long long a = cdst[v], c = csrc[v];
-          cand.id[slot] = (int32_t)v;
-          cand.gain[slot] = gain;
-          cand.cd[slot] = a;
-          cand.cs[slot] = c;
-          sum_cd += (unsigned long long)a;
-          sum_cs += (unsigned long long)c;
-          gmax = gain > gmax ? gain : gmax;
-          gmin = gain < gmin ? gain : gmin;
-          bytes += 16ull + 28ull;
-        }
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = tid; v < g.n; v += stride) {
+    bytes += 1;
+    if (part[v] != src) continue;
+    bytes += 12;
+    if (cand.stamp[v] == prev_tag) continue;  // stale: recomputed below
+    const long long gain = cand.gainv[v];
+    if (r < 0 || gain > 0) {
+      push_cand(cc, cand, (int32_t)v, gain, cdst[v], csrc[v], sum_cd, sum_cs, gmax, gmin);
+      bytes += 44;
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  const int32_t* dl = cand.dirty[(r < 0) ? 0 : (r & 1)];
+  for (int64_t k = tid >> 5; k < (int64_t)s_nd; k += stride >> 5) {
+    const int32_t v = dl[k];
+    const uint8_t p = part[v];
+    const int64_t b = g.start[v];
+    const int32_t d = g.deg[v];
+    long long acc = 0;
+    for (int32_t q = lane; q < d; q += 32) {
+      const long long w = g.W[b + q];
+      acc += (part[g.adj[b + q]] == p) ? -w : w;
+    }
+    acc = warp_sum64(acc);
+    if (lane == 0) {
+      cand.gainv[v] = acc;
+      bytes += 29ull + 13ull * (unsigned long long)d;
+      if (p == src && (r < 0 || acc > 0)) {
+        push_cand(cc, cand, v, acc, cdst[v], csrc[v], sum_cd, sum_cs, gmax, gmin);
+        bytes += 44;
       }
     }
   }
   sum_cd = block_sum<unsigned long long>(sum_cd, shu);
   sum_cs = block_sum<unsigned long long>(sum_cs, shu);
-  // block max / min via warp shuffles then shared
   {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -340,16 +390,19 @@ __global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, int64_t n,
       c.streak = (k == 0) ? c.streak + 1 : 0;
       if (c.streak == 2) c.done = 1;
       reset_counters(c.cc[par ^ 1]);  // the next round's counters (last read by round r-1)
+      c.ndirty[(r + 1) & 1] = 0;      // this round's apply stamps into it (last read by round r-1)
     } else {
       c.balanced = 1;
       c.bal_moves = k;
+      c.ndirty[0] = 0;
     }
   }
 }
 
+// Moves the accepted candidates and stamps them and their neighbours as stale for the next round
+// (a warp per candidate; atomicExch on the stamp lists each stale vertex once).
 __global__ void __launch_bounds__(256)
-    k_ref_apply(Ctl* ctl, int r, uint8_t* __restrict__ part, const int64_t* __restrict__ vC,
-                const int64_t* __restrict__ vG, Cands cand) {
+    k_ref_apply(Ctl* ctl, int r, LevelGraph g, uint8_t* __restrict__ part, int32_t tag, Cands cand) {
   __shared__ long long sh[32];
   __shared__ unsigned long long sacc[32];
   __shared__ int s_go;
@@ -371,23 +424,36 @@ __global__ void __launch_bounds__(256)
   if (!s_go) return;
   const int dst = 1 - s_src;
   const u128 thr = ((u128)s_hi << 64) | (u128)s_lo;
+  const int lane = threadIdx.x & 31;
+  unsigned long long* nd = &ctl->ndirty[(r + 1) & 1];
+  int32_t* dl = cand.dirty[(r + 1) & 1];
   long long dC = 0, dG = 0;
   unsigned long long bytes = 0;
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < s_N;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < (int64_t)s_N; i += nw) {
     const int32_t v = cand.id[i];
-    bytes += 12;
     if (s_accept == 2 && !(cand_key(s_gmax, cand.gain[i], v, s_idbits) < thr)) continue;
-    part[v] = (uint8_t)dst;
-    const long long c = vC[v], gg = vG[v];
-    bytes += 17;
-    if (dst == 1) {
-      dC -= c;
-      dG += gg;
-    } else {
-      dC += c;
-      dG -= gg;
+    if (lane == 0) {
+      part[v] = (uint8_t)dst;
+      const long long c = g.vC[v], gg = g.vG[v];
+      if (dst == 1) {
+        dC -= c;
+        dG += gg;
+      } else {
+        dC += c;
+        dG -= gg;
+      }
+      if (atomicExch(&cand.stamp[v], tag) != tag) dl[atomicAdd(nd, 1ull)] = v;
+      bytes += 29;
     }
+    const int64_t b = g.start[v];
+    const int32_t d = g.deg[v];
+    for (int32_t q = lane; q < d; q += 32) {
+      const int32_t u = g.adj[b + q];
+      if (atomicExch(&cand.stamp[u], tag) != tag) dl[atomicAdd(nd, 1ull)] = u;
+    }
+    if (lane == 0) bytes += 12ull + 8ull * (unsigned long long)d;
   }
   dC = block_sum<long long>(dC, sh);
   dG = block_sum<long long>(dG, sh);
@@ -431,18 +497,35 @@ void refine_loads(const LevelGraph& g, const uint8_t* part, Ctl* ctl, cudaStream
   GP_CHECK_LAUNCH();
 }
 
-void refine_level_run(const LevelGraph& g, uint8_t* part, Ctl* ctl, const Cands& cand, cudaStream_t s) {
+static inline int group_for_degree(double avg) {
+  if (avg <= 3.0) return 2;
+  if (avg <= 6.0) return 4;
+  if (avg <= 12.0) return 8;
+  if (avg <= 24.0) return 16;
+  return 32;
+}
+
+// One level: gains of all vertices, then the balance round and up to 8 gain rounds, enqueued without
+// host round trips (rounds after the stop return at once).  avg_deg selects the row group size.
+void refine_level_run(const LevelGraph& g, uint8_t* part, Ctl* ctl, const Cands& cand, int level, double avg_deg,
+                      cudaStream_t s) {
   const int64_t n = g.n;
-  const unsigned ggrid = grid_for((n + 31) / 32 * 32, 256);
+  const unsigned vgrid = grid_for(n, 256, 8);
   const unsigned agrid = grid_for(n, 256, 4);
+  const int G = group_for_degree(avg_deg);
+  switch (G) {
+#define GP_GA(GG) \
+  case GG: GP_LAUNCH(F_GAIN, k_gain_all<GG>, grid_for(n * GG, 256), 256, 0, s, g, part, cand.gainv); break;
+    GP_GA(2) GP_GA(4) GP_GA(8) GP_GA(16) GP_GA(32)
+#undef GP_GA
+  }
   GP_LAUNCH(F_MISC, k_ref_begin, 1, 1, 0, s, ctl, idbits_for(n));
-  GP_LAUNCH(F_GAIN, k_ref_gain, ggrid, 256, 0, s, g, part, ctl, -1, cand);
-  GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, -1, n, cand);
-  GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, -1, part, g.vC, g.vG, cand);
-  for (int r = 0; r < kRefineRounds; r++) {
-    GP_LAUNCH(F_GAIN, k_ref_gain, ggrid, 256, 0, s, g, part, ctl, r, cand);
+  int32_t prev = round_tag(level, -2);  // no stale vertices before the balance round
+  for (int r = -1; r < kRefineRounds; r++) {
+    GP_LAUNCH(F_GAIN, k_ref_cands, vgrid, 256, 0, s, g, part, ctl, r, prev, cand);
     GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, r, n, cand);
-    GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, r, part, g.vC, g.vG, cand);
+    GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, r, g, part, round_tag(level, r), cand);
+    prev = round_tag(level, r);
   }
   GP_CHECK_LAUNCH();
 }

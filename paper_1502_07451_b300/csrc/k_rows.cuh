@@ -398,6 +398,96 @@ __global__ void __launch_bounds__(kHugeThreads)
   account(fam, bytes, sacc);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Unordered merge (contraction): duplicates are combined in a per-warp shared-memory hash table and
+// the distinct (column, summed weight) pairs are written in table order.  Every consumer of coarse
+// rows is independent of their order (sums, maxima under a total order, sets); the two-hop pairing
+// sorts what it walks.  Rows longer than TMAX / 2 raw entries are deferred to the next tier.
+// ------------------------------------------------------------------------------------------------
+constexpr int32_t kEmptyKey = -1;
+
+template <int TMAX, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+    k_merge_hash(TwoSrc s, int64_t nrows, const int32_t* __restrict__ list, const unsigned* list_cnt,
+                 const int64_t* __restrict__ out_start, int32_t* __restrict__ deg_out,
+                 int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int32_t* __restrict__ dl1,
+                 unsigned* dc1, int64_t split1, int32_t* __restrict__ dl2, unsigned* dc2, int64_t split2,
+                 int32_t* __restrict__ dl3, unsigned* dc3, int fam) {
+  extern __shared__ __align__(16) unsigned char smem_h[];
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned long long* V = (unsigned long long*)smem_h + (size_t)wib * TMAX;
+  int32_t* K = (int32_t*)((unsigned long long*)smem_h + (size_t)WARPS * TMAX) + (size_t)wib * TMAX;
+  const unsigned lt = lanemask_lt();
+  const int64_t total = list ? (int64_t)*list_cnt : nrows;
+  unsigned long long bytes = 0;
+  for (int64_t it = (int64_t)blockIdx.x * WARPS + wib; it < total; it += (int64_t)gridDim.x * WARPS) {
+    const int64_t r = list ? (int64_t)list[it] : it;
+    const RowView v = row_view(s, r);
+    const int64_t len = v.a_len + v.b_len;
+    if (2 * len > TMAX) {
+      if (lane == 0) {
+        if (len <= split1)
+          dl1[atomicAdd(dc1, 1u)] = (int32_t)r;
+        else if (len <= split2)
+          dl2[atomicAdd(dc2, 1u)] = (int32_t)r;
+        else
+          dl3[atomicAdd(dc3, 1u)] = (int32_t)r;
+      }
+      continue;
+    }
+    int T = 32;
+    while (T < 2 * len) T <<= 1;
+    const int shift = 32 - (31 - __clz(T));
+    for (int i = lane; i < T; i += 32) {
+      K[i] = kEmptyKey;
+      V[i] = 0ull;
+    }
+    __syncwarp();
+    for (int64_t i = lane; i < len; i += 32) {
+      int32_t col;
+      int64_t w;
+      row_entry(s, v, i, col, w);
+      bytes += entry_bytes(s, i < v.a_len);
+      if (s.drop_self && col == (int32_t)r) continue;
+      unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+      for (;;) {
+        const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+        if (old == kEmptyKey || old == col) {
+          atomicAdd(&V[slot], (unsigned long long)w);
+          break;
+        }
+        slot = (slot + 1) & (unsigned)(T - 1);
+      }
+    }
+    __syncwarp();
+    const int64_t ob = out_start[r];
+    int out = 0;
+    for (int base = 0; base < T; base += 32) {
+      const int32_t k = K[base + lane];
+      const bool has = k != kEmptyKey;
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      if (has) {
+        const int pos = out + __popc(m & lt);
+        adj_out[ob + pos] = k;
+        W_out[ob + pos] = (int64_t)V[base + lane];
+      }
+      out += __popc(m);
+    }
+    if (lane == 0) {
+      deg_out[r] = out;
+      bytes += 12ull * (unsigned long long)out + 24ull;
+    }
+    __syncwarp();
+  }
+  account(fam, bytes, sacc);
+}
+
+constexpr int kHashT1 = 256, kHashW1 = 8;    // rows of <= 128 raw entries
+constexpr int kHashT2 = 2048, kHashW2 = 4;   // rows of <= 1024 raw entries
+constexpr size_t kHashSmem1 = (size_t)kHashT1 * kHashW1 * 12;
+constexpr size_t kHashSmem2 = (size_t)kHashT2 * kHashW2 * 12;
+
 void merge_rows(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* out_start,
                 int32_t* deg_out, int32_t* adj_out, int64_t* W_out, int family, int64_t raw_bound,
                 cudaStream_t s) {
@@ -430,6 +520,50 @@ void merge_rows(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* 
   dfree(tv, s);
   dfree(list_mid, s);
   dfree(list_huge, s);
+  dfree(cnts, s);
+}
+
+// Contraction merge: rows in no particular order (see k_merge_hash).
+void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* out_start,
+                          int32_t* deg_out, int32_t* adj_out, int64_t* W_out, int family, int64_t raw_bound,
+                          cudaStream_t s) {
+  if (nrows <= 0) return;
+  static bool attr_set = false;
+  if (!attr_set) {
+    GP_CUDA(cudaFuncSetAttribute(k_merge_hash<kHashT2, kHashW2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHashSmem2));
+    GP_CUDA(cudaFuncSetAttribute(k_merge_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kMergeBlockSmem));
+    attr_set = true;
+  }
+  unsigned* cnts = dnew<unsigned>(4, s);  // tier-2 list, tier-3 list, huge list, unused
+  GP_CUDA(cudaMemsetAsync(cnts, 0, 4 * sizeof(unsigned), s));
+  int32_t* l2 = dnew<int32_t>(nrows, s);
+  int32_t* l3 = dnew<int32_t>(nrows, s);
+  int32_t* lh = dnew<int32_t>(nrows, s);
+  const int sms = num_sms();
+  const int64_t want = (nrows + kHashW1 - 1) / kHashW1;
+  const unsigned grid1 = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
+  GP_LAUNCH(family, (k_merge_hash<kHashT1, kHashW1>), grid1, kHashW1 * 32, kHashSmem1, s, src, nrows,
+            (const int32_t*)nullptr, (const unsigned*)nullptr, out_start, deg_out, adj_out, W_out, l2, cnts,
+            (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
+  GP_LAUNCH(family, (k_merge_hash<kHashT2, kHashW2>), (unsigned)(2 * sms), kHashW2 * 32, kHashSmem2, s, src,
+            nrows, (const int32_t*)l2, (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, l2, cnts,
+            (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
+  GP_LAUNCH(family, k_merge_block, (unsigned)(2 * sms), kMergeBlockThreads, kMergeBlockSmem, s, src, l3, cnts + 1,
+            out_start, deg_out, adj_out, W_out, family);
+  int nbits = 1;
+  while (nbits < 31 && (int64_t(1) << nbits) < ncols) nbits++;
+  int32_t* tk = dnew<int32_t>(raw_bound, s);
+  int64_t* tv = dnew<int64_t>(raw_bound, s);
+  GP_LAUNCH(family, k_merge_huge, (unsigned)sms, kHugeThreads, 0, s, src, lh, cnts + 2, out_start, deg_out, adj_out,
+            W_out, tk, tv, nbits, family);
+  GP_CHECK_LAUNCH();
+  dfree(tk, s);
+  dfree(tv, s);
+  dfree(l2, s);
+  dfree(l3, s);
+  dfree(lh, s);
   dfree(cnts, s);
 }
 
