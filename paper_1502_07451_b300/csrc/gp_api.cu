@@ -90,7 +90,7 @@ static void prof_collect() {
   g_ev.clear();
 }
 
-int cluster_max(const void* fn, int block) {
+int cluster_max(const void* fn, int block, size_t smem) {
   static std::mutex mu;
   static std::vector<std::pair<std::pair<const void*, int>, int>> cache;  // ((fn, device), size)
   const int dev = device_id();
@@ -106,6 +106,7 @@ int cluster_max(const void* fn, int block) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)cs);
     cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = (unsigned)cs;
@@ -121,6 +122,7 @@ int cluster_max(const void* fn, int block) {
     cudaGetLastError();
   }
   cache.push_back({{fn, dev}, best});
+  if (getenv("GP_LOG")) fprintf(stderr, "[gp] cluster size %d for %p (block %d, smem %zu)\n", best, fn, block, smem);
   return best;
 }
 
@@ -280,11 +282,11 @@ static cudaError_t launch_makespan(const gp_graph* g, const uint8_t* part, unsig
   switch (G) {
 #define GP_MS(GG)                                                                                      \
   case GG: {                                                                                           \
-    const int cmax = cluster_max((const void*)k_makespan<GG>, 1024);                                   \
+    const int cmax = cluster_max((const void*)k_makespan<GG>, 1024, 0);                                \
     if (cmax <= 0) return cudaErrorLaunchFailure;                                                      \
     int64_t want = (g->max_width * GG + 1023) / 1024;                                                  \
     const int cs = (int)(want < 1 ? 1 : (want < cmax ? want : cmax));                                  \
-    return launch_cluster(F_MAKESPAN, k_makespan<GG>, cs, 1024, s, nlev, (const int64_t*)g->lev_ptr,    \
+    return launch_cluster(F_MAKESPAN, k_makespan<GG>, cs, 1024, 0, s, nlev, (const int64_t*)g->lev_ptr, \
                           (const int32_t*)g->lev_vtx, (const int64_t*)g->lo_off, (const int32_t*)g->lo_src, \
                           (const int32_t*)g->lo_w, (const int32_t*)g->lo_cC, (const int32_t*)g->lo_cG, part, \
                           fp, ms, bad, fin);                                                           \
@@ -431,9 +433,9 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
       switch (G) {
 #define GP_LEV(GG)                                                                                       \
   case GG: {                                                                                            \
-    const int cs = cluster_max((const void*)k_levels<GG>, 1024);                                        \
+    const int cs = cluster_max((const void*)k_levels<GG>, 1024, 0);                                     \
     if (cs > 0) {                                                                                       \
-      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, s, nn, (const int64_t*)g->off,            \
+      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, s, nn, (const int64_t*)g->off,         \
                              (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->lev_ptr, \
                              g->level, tail, nlev_dev));                                                \
       ok = 1;                                                                                           \
@@ -496,7 +498,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     src.b_col = in_src;
     src.b_w32 = in_w;
     src.drop_self = 0;
-    merge_rows(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s);
+    merge_rows_unordered(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s);
     unsigned long long* a0 = A.get<unsigned long long>(1);
     GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
     if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, s, n, L.deg, a0);
@@ -541,9 +543,19 @@ gp_status gp_graph_export(const gp_graph* g, int64_t* off, int32_t* adj, int64_t
     int64_t* coff = A.get<int64_t>(n + 1);
     int32_t* cadj = A.get<int32_t>(g->a0);
     int64_t* cW = A.get<int64_t>(g->a0);
-    scan_i32_to_i64(g->L0.deg, coff, n, s);
-    if (n) GP_LAUNCH(F_MISC, k_compact_rows, grid_for(n * 32, 256), 256, 0, s, n, g->L0.start, g->L0.deg, g->L0.adj,
-                     g->L0.W, coff, cadj, cW);
+    // level-0 rows are kept in no particular order; sort them (by neighbour) for the export
+    int32_t* sdeg = A.get<int32_t>(n);
+    int32_t* sadj = A.get<int32_t>(g->L0.cap);
+    int64_t* sW = A.get<int64_t>(g->L0.cap);
+    TwoSrc src{};
+    src.a_start = g->L0.start;
+    src.a_deg = g->L0.deg;
+    src.a_col = g->L0.adj;
+    src.a_w64 = g->L0.W;
+    merge_rows(src, n, n, g->L0.start, sdeg, sadj, sW, F_MISC, g->L0.cap, s);
+    scan_i32_to_i64(sdeg, coff, n, s);
+    if (n) GP_LAUNCH(F_MISC, k_compact_rows, grid_for(n * 32, 256), 256, 0, s, n, g->L0.start, sdeg, sadj, sW, coff,
+                     cadj, cW);
     GP_CHECK_LAUNCH();
     if (off) GP_CUDA(cudaMemcpyAsync(off, coff, sizeof(int64_t) * (n + 1), cudaMemcpyDefault, s));
     if (adj && g->a0) GP_CUDA(cudaMemcpyAsync(adj, cadj, sizeof(int32_t) * g->a0, cudaMemcpyDefault, s));

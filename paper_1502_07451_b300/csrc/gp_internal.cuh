@@ -170,21 +170,45 @@ __device__ __forceinline__ void account(int fam, unsigned long long bytes_this_t
 // of up to 16 CTAs x 1024 threads and separate levels with the hardware cluster barrier; data that
 // other CTAs wrote before the barrier is read with L2-only loads (__ldcg).
 // ------------------------------------------------------------------------------------------------
+// Bulk L2 prefetch of [p, p + bytes) spread over the threads of the grid (16-byte aligned chunks of
+// up to 64 KiB; the unaligned head and tail are left to demand loads).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a0 = ((uintptr_t)p + 15) & ~(uintptr_t)15;
+  const uintptr_t a1 = ((uintptr_t)p + bytes) & ~(uintptr_t)15;
+  if (a1 <= a0) return;
+  constexpr uintptr_t kChunk = 65536;
+  const uintptr_t nch = (a1 - a0 + kChunk - 1) / kChunk;
+  const uintptr_t tid = (uintptr_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uintptr_t nt = (uintptr_t)gridDim.x * blockDim.x;
+  for (uintptr_t c = tid; c < nch; c += nt) {
+    const uintptr_t s = a0 + c * kChunk;
+    const uintptr_t e = (s + kChunk < a1) ? s + kChunk : a1;
+    const unsigned sz = (unsigned)(e - s);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"(sz) : "memory");
+  }
+}
+
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;\n" ::: "memory");
 }
+// Split form: work placed between arrive and wait overlaps the barrier.  The release waits for the
+// thread's earlier memory operations, so loads issued after the arrive do not delay it.
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory"); }
 
 // Largest cluster (16 if the device allows non-portable sizes, else 8) that can be resident for
 // `fn` with `block` threads per CTA; 0 if none.
-int cluster_max(const void* fn, int block);
+int cluster_max(const void* fn, int block, size_t smem);
 
 template <typename... KArgs, typename... Args>
-cudaError_t launch_cluster(int family, void (*kern)(KArgs...), int csize, int block, cudaStream_t s,
+cudaError_t launch_cluster(int family, void (*kern)(KArgs...), int csize, int block, size_t smem, cudaStream_t s,
                            Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)csize);
   cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

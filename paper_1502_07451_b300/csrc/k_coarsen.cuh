@@ -28,33 +28,76 @@ __global__ void k_match_init(int64_t n, const int64_t* __restrict__ vC, const in
   }
 }
 
+// max vertex weights of the level (vC, vG >= 0): a vertex v with vC[v] + maxC <= capC and
+// vG[v] + maxG <= capG fits the caps with any neighbour, so its picks skip the weight gathers.
+__global__ void k_max_weights(int64_t n, const int64_t* __restrict__ vC, const int64_t* __restrict__ vG,
+                              long long* mx) {
+  long long a = 0, b = 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    a = vC[v] > a ? vC[v] : a;
+    b = vG[v] > b ? vG[v] : b;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long x = __shfl_xor_sync(0xffffffffu, a, o), y = __shfl_xor_sync(0xffffffffu, b, o);
+    a = x > a ? x : a;
+    b = y > b ? y : b;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (a) atomicMax(&mx[0], a);
+    if (b) atomicMax(&mx[1], b);
+  }
+}
+
+__device__ __forceinline__ EdgeKey group_best_key(EdgeKey k, unsigned gmask, int G) {
+  for (int o = G / 2; o > 0; o >>= 1) {
+    EdgeKey q;
+    q.W = __shfl_xor_sync(gmask, k.W, o, G);
+    q.h = __shfl_xor_sync(gmask, k.h, o, G);
+    q.nm = __shfl_xor_sync(gmask, k.nm, o, G);
+    if (key_better(q, k)) k = q;
+  }
+  return k;
+}
+
+__device__ __forceinline__ unsigned group_mask(int G) {
+  return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+}
+
+// One handshake round, picks: a group of G lanes per unmatched vertex.
+template <int G>
 __global__ void __launch_bounds__(256)
-    k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const int32_t* __restrict__ mate,
-                 int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
+    k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const long long* __restrict__ maxw,
+                 const int32_t* __restrict__ mate, int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
   __shared__ unsigned long long sacc[32];
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int sub = threadIdx.x % G;
+  const unsigned gmask = group_mask(G);
+  const long long mC = maxw[0], mG = maxw[1];
   unsigned long long bytes = 0;
-  for (int64_t v = gw; v < g.n; v += nw) {
-    if (lane == 0) bytes += 5;
-    if (mate[v] != -1 || !alive[v]) continue;
+  for (int64_t v = group; v < g.n; v += ngroups) {
+    if (sub == 0) bytes += 5;
+    if (mate[v] != -1 || !alive[v]) continue;  // same v across the group: uniform
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
     const int64_t cv = g.vC[v], gv = g.vG[v];
+    const bool nocap = cv + mC <= capC && gv + mG <= capG;
     EdgeKey best = key_none();
-    for (int32_t k = lane; k < d; k += 32) {
+    for (int32_t k = sub; k < d; k += G) {
       const int32_t u = g.adj[b + k];
       bytes += 8;
       if (mate[u] != -1) continue;
-      const int64_t cu = g.vC[u], gu = g.vG[u];
-      bytes += 24;
-      if (cv + cu > capC || gv + gu > capG) continue;
+      if (!nocap) {
+        bytes += 16;
+        if (cv + g.vC[u] > capC || gv + g.vG[u] > capG) continue;
+      }
+      bytes += 8;
       const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)u);
       if (key_better(kk, best)) best = kk;
     }
-    best = warp_best_key(best);
-    if (lane == 0) {
+    best = group_best_key(best, gmask, G);
+    if (sub == 0) {
       bytes += 12 + 16 + 4;
       if (best.W < 0) {
         pick[v] = -1;
@@ -76,17 +119,19 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
 }
 
 // anchor of every unmatched vertex: its best neighbour under the matching key (no filters)
+template <int G>
 __global__ void __launch_bounds__(256)
     k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
              uint8_t* __restrict__ is_anchor) {
   __shared__ unsigned long long sacc[32];
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int sub = threadIdx.x % G;
+  const unsigned gmask = group_mask(G);
   unsigned long long bytes = 0;
-  for (int64_t v = gw; v < g.n; v += nw) {
+  for (int64_t v = group; v < g.n; v += ngroups) {
     if (mate[v] != -1) {
-      if (lane == 0) {
+      if (sub == 0) {
         anchor[v] = -1;
         bytes += 8;
       }
@@ -95,13 +140,13 @@ __global__ void __launch_bounds__(256)
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
     EdgeKey best = key_none();
-    for (int32_t k = lane; k < d; k += 32) {
+    for (int32_t k = sub; k < d; k += G) {
       const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)g.adj[b + k]);
       if (key_better(kk, best)) best = kk;
       bytes += 12;
     }
-    best = warp_best_key(best);
-    if (lane == 0) {
+    best = group_best_key(best, gmask, G);
+    if (sub == 0) {
       bytes += 20;
       if (best.W < 0) {
         anchor[v] = -1;
@@ -193,57 +238,137 @@ __device__ __forceinline__ void warp_bitonic_keys(int32_t* K, int P, int lane) {
 }
 
 constexpr int kSatCap = 1024;  // anchored vertices a warp sorts in shared memory
-constexpr int kTwohopWarps = 8;
+constexpr int kTwohopWarps = 4;
+
+// Sorts k <= 32 keys held one per lane (ascending; lanes >= k hold INT32_MAX).
+__device__ __forceinline__ int32_t warp_sort32(int32_t x, int lane) {
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+      const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
+      x = keep_min ? (x < y ? x : y) : (x > y ? x : y);
+    }
+  }
+  return x;
+}
+
+// Stable LSD radix sort of k keys in [0, 2^nbits) by one warp (8-bit digits), ping-ponging between
+// A and B; returns the buffer holding the sorted keys.
+__device__ int32_t* warp_radix_keys(int32_t* A, int32_t* B, int k, int nbits, int* hist) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  for (int shift = 0; shift < nbits; shift += 8) {
+    for (int d = lane; d < 256; d += 32) hist[d] = 0;
+    __syncwarp();
+    for (int i = lane; i < k; i += 32) atomicAdd(&hist[(A[i] >> shift) & 255], 1);
+    __syncwarp();
+    int loc[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      loc[q] = hist[8 * lane + q];
+      sum += loc[q];
+    }
+    int inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    int run = inc - sum;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      hist[8 * lane + q] = run;
+      run += loc[q];
+    }
+    __syncwarp();
+    for (int base = 0; base < k; base += 32) {
+      const int i = base + lane;
+      const bool valid = i < k;
+      const int32_t key = valid ? A[i] : 0;
+      const int d = (key >> shift) & 255;
+      const unsigned act = __ballot_sync(0xffffffffu, valid);
+      unsigned peers = 0;
+      int pos0 = 0, rank = 0;
+      if (valid) {
+        peers = __match_any_sync(act, d);
+        rank = __popc(peers & lt);
+        pos0 = hist[d];
+      }
+      __syncwarp();
+      if (valid) {
+        B[pos0 + rank] = key;
+        if (rank == 0) hist[d] = pos0 + __popc(peers);
+      }
+      __syncwarp();
+    }
+    int32_t* t = A;
+    A = B;
+    B = t;
+  }
+  return A;
+}
 
 // Warp per anchor: gathers its anchored vertices (rows are in no particular order), sorts them and
 // pairs them.  Anchors with more than kSatCap of them go to a list for k_twohop_big.
 __global__ void __launch_bounds__(kTwohopWarps * 32)
     k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
              const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate, int32_t* __restrict__ big,
-             unsigned* big_cnt) {
-  __shared__ int32_t sat[kTwohopWarps][kSatCap];
+             unsigned* big_cnt, int nbits) {
+  __shared__ int32_t sat[kTwohopWarps][2][kSatCap];
+  __shared__ int hist_all[kTwohopWarps][256];
   __shared__ unsigned long long sacc[32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = lanemask_lt();
-  int32_t* S = sat[wib];
+  int32_t* S = sat[wib][0];
   const int64_t gw = (int64_t)blockIdx.x * kTwohopWarps + wib;
   const int64_t nw = (int64_t)gridDim.x * kTwohopWarps;
   unsigned long long bytes = 0;
-  for (int64_t h = gw; h < g.n; h += nw) {
-    if (!is_anchor[h]) continue;
-    const int64_t b = g.start[h];
-    const int32_t d = g.deg[h];
-    int k = 0;
-    bool over = false;
-    for (int32_t base = 0; base < d && !over; base += 32) {
-      const int32_t q = base + lane;
-      int32_t v = -1;
-      bool flag = false;
-      if (q < d) {
-        v = g.adj[b + q];
-        flag = anchor[v] == (int32_t)h;
-        bytes += 8;
+  for (int64_t hb = gw * 32; hb < g.n; hb += nw * 32) {
+    unsigned am = __ballot_sync(0xffffffffu, hb + lane < g.n && is_anchor[hb + lane]);
+    while (am) {
+      const int64_t h = hb + __ffs(am) - 1;
+      am &= am - 1;
+      const int64_t b = g.start[h];
+      const int32_t d = g.deg[h];
+      int k = 0;
+      bool over = false;
+      for (int32_t base = 0; base < d; base += 32) {
+        const int32_t q = base + lane;
+        int32_t v = -1;
+        bool flag = false;
+        if (q < d) {
+          v = g.adj[b + q];
+          flag = anchor[v] == (int32_t)h;
+          bytes += 8;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (k + __popc(m) > kSatCap) {
+          over = true;
+          break;
+        }
+        if (flag) S[k + __popc(m & lt)] = v;
+        k += __popc(m);
       }
-      const unsigned m = __ballot_sync(0xffffffffu, flag);
-      if (k + __popc(m) > kSatCap) {
-        over = true;
-        break;
+      if (over) {
+        if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
+        continue;
       }
-      if (flag) S[k + __popc(m & lt)] = v;
-      k += __popc(m);
+      if (k == 0) continue;
+      __syncwarp();
+      const int32_t* sorted = S;
+      if (k <= 32) {
+        const int32_t x = warp_sort32(lane < k ? S[lane] : INT32_MAX, lane);
+        __syncwarp();
+        S[lane] = x;
+        __syncwarp();
+      } else {
+        sorted = warp_radix_keys(S, sat[wib][1], k, nbits, hist_all[wib]);
+      }
+      pair_sorted(g, capC, capG, sorted, k, mate, bytes);
+      __syncwarp();
     }
-    if (over) {
-      if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
-      continue;
-    }
-    if (k == 0) continue;
-    int P = 32;
-    while (P < k) P <<= 1;
-    for (int i = k + lane; i < P; i += 32) S[i] = INT32_MAX;
-    __syncwarp();
-    warp_bitonic_keys(S, P, lane);
-    pair_sorted(g, capC, capG, S, k, mate, bytes);
-    __syncwarp();
   }
   account(F_TWOHOP, bytes, sacc);
 }
@@ -368,16 +493,35 @@ static inline unsigned grid_for(int64_t work, int per_block, int max_per_sm = 16
   return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
+static inline int group_for_avg(double avg) {
+  if (avg <= 3.0) return 2;
+  if (avg <= 6.0) return 4;
+  if (avg <= 12.0) return 8;
+  if (avg <= 24.0) return 16;
+  return 32;
+}
+
 void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, int rounds, bool twohop,
                  int32_t* mate, cudaStream_t s) {
   const int64_t n = g.n;
   if (n <= 0) return;
   int32_t* pick = dnew<int32_t>(n, s);
   uint8_t* alive = dnew<uint8_t>(n, s);
+  long long* maxw = dnew<long long>(2, s);
+  const int G = group_for_avg((double)g.cap / (double)n);
+  GP_CUDA(cudaMemsetAsync(maxw, 0, 2 * sizeof(long long), s));
   GP_LAUNCH(F_MISC, k_match_init, grid_for(n, 256), 256, 0, s, n, g.vC, g.vG, capC, capG, mate, pick, alive);
+  GP_LAUNCH(F_MISC, k_max_weights, grid_for(n, 256, 4), 256, 0, s, n, g.vC, g.vG, maxw);
   for (int r = 0; r < rounds; r++) {
-    GP_LAUNCH(F_MATCH_PICK, k_match_pick, grid_for(n * 32, 256), 256, 0, s, g, capC, capG, seed, mate, pick,
-              alive);
+    switch (G) {
+#define GP_MP(GG)                                                                                       \
+  case GG:                                                                                             \
+    GP_LAUNCH(F_MATCH_PICK, k_match_pick<GG>, grid_for(n * GG, 256), 256, 0, s, g, capC, capG, seed,    \
+              (const long long*)maxw, mate, pick, alive);                                              \
+    break;
+      GP_MP(2) GP_MP(4) GP_MP(8) GP_MP(16) GP_MP(32)
+#undef GP_MP
+    }
     GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick);
   }
   if (twohop) {
@@ -389,11 +533,18 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
     int32_t* tb = dnew<int32_t>(g.cap, s);
     GP_CUDA(cudaMemsetAsync(is_anchor, 0, (size_t)n, s));
     GP_CUDA(cudaMemsetAsync(big_cnt, 0, sizeof(unsigned), s));
-    GP_LAUNCH(F_TWOHOP, k_anchor, grid_for(n * 32, 256), 256, 0, s, g, seed, mate, anchor, is_anchor);
-    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n, kTwohopWarps, 16), kTwohopWarps * 32, 0, s, g, capC, capG, anchor,
-              is_anchor, mate, big, big_cnt);
+    switch (G) {
+#define GP_AN(GG)                                                                                         \
+  case GG:                                                                                               \
+    GP_LAUNCH(F_TWOHOP, k_anchor<GG>, grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor, is_anchor); \
+    break;
+      GP_AN(2) GP_AN(4) GP_AN(8) GP_AN(16) GP_AN(32)
+#undef GP_AN
+    }
     int nbits = 1;
     while (nbits < 31 && (int64_t(1) << nbits) < n) nbits++;
+    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n, kTwohopWarps * 32, 16), kTwohopWarps * 32, 0, s, g, capC, capG,
+              anchor, is_anchor, mate, big, big_cnt, nbits);
     GP_LAUNCH(F_TWOHOP, k_twohop_big, (unsigned)num_sms(), 1024, 0, s, g, capC, capG, anchor, mate, big, big_cnt,
               ta, tb, nbits);
     dfree(big_cnt, s);
@@ -404,6 +555,7 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
   GP_CHECK_LAUNCH();
   dfree(pick, s);
   dfree(alive, s);
+  dfree(maxw, s);
 }
 
 void coarse_count(const LevelGraph& g, const int32_t* mate, int32_t* cmap, int64_t* /*unused*/, cudaStream_t s) {

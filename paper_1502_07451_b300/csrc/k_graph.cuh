@@ -88,6 +88,8 @@ __global__ void __launch_bounds__(1024)
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = (int)(tid % G);
+  prefetch_l2(off, sizeof(int64_t) * (size_t)(n + 1));  // the level loop chases these: keep them in L2
+  prefetch_l2(cols, sizeof(int32_t) * (size_t)off[n]);
   for (int64_t v = tid; v < n; v += stride) {
     const int32_t d = (int32_t)(in_off[v + 1] - in_off[v]);
     rem[v] = d;
@@ -109,12 +111,28 @@ __global__ void __launch_bounds__(1024)
     for (int64_t i = beg + group; i < end; i += ngroups) {
       const int32_t v = __ldcg(lev_vtx + i);  // written by other CTAs: bypass L1
       const int64_t eb = off[v], ee = off[v + 1];
-      for (int64_t e = eb + sub; e < ee; e += G) {
-        const int32_t u = cols[e];
-        if (atomicSub(&rem[u], 1) == 1) {
-          const unsigned long long k = atomicAdd(app, 1ull);
-          lev_vtx[end + (int64_t)k] = u;
-          level[u] = lev + 1;
+      // two out-entries per lane at a time: both decrements are in flight together
+      for (int64_t e = eb + sub; e < ee; e += 2 * G) {
+        const bool two = e + G < ee;
+        const int32_t u1 = cols[e];
+        const int32_t u2 = two ? cols[e + G] : -1;
+        const int r1 = atomicSub(&rem[u1], 1);
+        const int r2 = two ? atomicSub(&rem[u2], 1) : 0;
+#pragma unroll
+        for (int q = 0; q < 2; q++) {
+          const int32_t u = q ? u2 : u1;
+          if ((q ? r2 : r1) == 1) {
+            // warp-aggregated append: one atomic per set of lanes that got here together
+            const unsigned act = __activemask();
+            const int lane = threadIdx.x & 31;
+            const int leader = __ffs(act) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(app, (unsigned long long)__popc(act));
+            base = __shfl_sync(act, base, leader);
+            const unsigned long long k = base + (unsigned long long)__popc(act & ((1u << lane) - 1u));
+            lev_vtx[end + (int64_t)k] = u;
+            level[u] = lev + 1;
+          }
         }
       }
     }
