@@ -169,6 +169,50 @@ GP_API gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* ma
 GP_API gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part, int64_t* makespan,
                                      int64_t* finish_out, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * gp_batch_partition -- gp_partition for `count` graphs in one call.  The paper's scheduler makes
+ * its decision offline, one DAG at a time (Sec. IV.D); a scheduler serving many DAGs makes many
+ * such decisions, and this entry point makes them together (the paper has no batched form).  Graph i gets exactly what
+ * gp_partition(graphs[i], r_cpu[i], tol, seeds[i], parts[i], &res[i], stream) would give it (same
+ * split, cut, loads, levels, rounds and coarsest size; ms[] differs).  The graphs run in one
+ * persistent kernel launch, replayed from a captured CUDA graph: a CTA takes one graph at a time,
+ * largest first, and runs every step of the partition on it.  Graphs with more than 2^23
+ * adjacency entries, and graphs whose coarse levels outgrow a CTA's workspace, are partitioned by
+ * the single-graph path within the same call.
+ *   count       number of graphs (>= 0)
+ *   graphs      `count` handles, all on the current device
+ *   r_cpu       `count` CPU shares as in gp_partition, or NULL (all -1: Eq. (1) from the sums)
+ *   tol         balance tolerance in [0, 1], shared by all graphs
+ *   seeds       `count` seeds, or NULL (all 0)
+ *   parts       `count` pointers to uint8[n_i] buffers (device or host memory; entries of graphs
+ *               with n_i = 0 may be NULL); receive the splits
+ *   res         `count` results (host), or NULL; res[i].ms[0] = the persistent kernel's time
+ *   makespans   `count` int64 (host) receiving the makespan of each final split (as gp_makespan),
+ *               or NULL (the makespan pass is then skipped)
+ * The call returns when every output is written (it synchronises `stream`).  Calls on one device
+ * are serialised internally.  Errors: GP_ERR_INVALID (arguments, checked before any work),
+ * GP_ERR_OOM, GP_ERR_CUDA.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_batch_partition(int32_t count, gp_graph* const* graphs, const double* r_cpu, double tol,
+                                    const uint64_t* seeds, uint8_t* const* parts, gp_result* res,
+                                    int64_t* makespans, void* stream);
+
+/* Schedules of the batch kernel (threads per CTA, CTAs per SM, lanes per adjacency row, hash-table
+ * size).  A schedule changes only the speed, never a result.
+ *   gp_batch_schedule_count: how many there are; gp_batch_schedule_name(i): a short name (NULL
+ *   past the last).
+ *   gp_batch_set_schedule(i): use schedule i in later calls; -1 restores the default (the
+ *   autotuned choice of the device if there is one, else schedule 0).
+ *   gp_batch_autotune: runs the batch (arguments as gp_batch_partition; results discarded) once
+ *   per schedule after a warm-up run, keeps the fastest as the device's choice, writes its index to
+ *   *best and each schedule's kernel time in ms to ms_out[0 .. gp_batch_schedule_count()-1] (if
+ *   ms_out != NULL).  Errors as gp_batch_partition. */
+GP_API int32_t gp_batch_schedule_count(void);
+GP_API const char* gp_batch_schedule_name(int32_t i);
+GP_API gp_status gp_batch_set_schedule(int32_t i);
+GP_API gp_status gp_batch_autotune(int32_t count, gp_graph* const* graphs, const double* r_cpu, double tol,
+                                   const uint64_t* seeds, int32_t* best, float* ms_out, void* stream);
+
 /* Cut of a split: sum of edge costs of directed edges whose ends are on different sides. */
 GP_API gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* stream);
 

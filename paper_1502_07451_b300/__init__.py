@@ -95,6 +95,9 @@ def lib():
                 "gp_prof_enable": [C.c_int],
                 "gp_prof_reset": [],
                 "gp_prof_read": [C.c_int, _P, _P, _P],
+                "gp_batch_partition": [_I32, _P, _P, _D, _P, _P, _P, _P, _P],
+                "gp_batch_set_schedule": [_I32],
+                "gp_batch_autotune": [_I32, _P, _P, _D, _P, _P, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -106,6 +109,10 @@ def lib():
             L.gp_kernel_name.restype = C.c_char_p
             L.gp_launch_count.argtypes = []
             L.gp_launch_count.restype = C.c_int64
+            L.gp_batch_schedule_count.argtypes = []
+            L.gp_batch_schedule_count.restype = C.c_int32
+            L.gp_batch_schedule_name.argtypes = [_I32]
+            L.gp_batch_schedule_name.restype = C.c_char_p
             _lib = L
     return _lib
 
@@ -279,6 +286,57 @@ def gp_step_refine(n, off, adj, W, vC, vG, bound_cpu, bound_gpu, part, stream=No
                                 int(bound_cpu), int(bound_gpu), _ptr(part)[0], st, _stream(stream)),
            "gp_step_refine")
     return dict(rounds=st[0], balanced=st[1], moves=st[2], bal_moves=st[3], load_cpu=st[4], load_gpu=st[5])
+
+
+def _batch_args(handles, r_cpu, seeds):
+    count = len(handles)
+    hs = (_P * max(count, 1))(*[h.value if isinstance(h, _P) else h for h in handles])
+    rc = None if r_cpu is None else (_D * max(count, 1))(*[float(x) for x in r_cpu])
+    sd = None if seeds is None else (_U64 * max(count, 1))(*[int(x) for x in seeds])
+    return count, hs, rc, sd
+
+
+def gp_batch_partition(handles, parts, r_cpu=None, tol=0.03, seeds=None, makespans=False, stream=None):
+    """Partition many graphs in one call (one persistent launch); returns (results, makespans).
+
+    handles: graph handles; parts: one uint8 buffer per graph (device tensors or host arrays);
+    r_cpu / seeds: per-graph lists or None (-1 / 0 for all).  makespans=True also evaluates the
+    makespan of every final split.
+    """
+    count, hs, rc, sd = _batch_args(handles, r_cpu, seeds)
+    if len(parts) != count:
+        raise ValueError("one split buffer per graph")
+    pp = (_P * max(count, 1))(*[_ptr(p)[0] for p in parts])
+    res = (Result * max(count, 1))()
+    ms = (C.c_int64 * max(count, 1))() if makespans else None
+    _check(lib().gp_batch_partition(count, hs, rc, float(tol), sd, pp, res, ms, _stream(stream)),
+           "gp_batch_partition")
+    out = [res[i].as_dict() for i in range(count)]
+    return out, ([int(ms[i]) for i in range(count)] if makespans else None)
+
+
+def gp_batch_schedule_count() -> int:
+    return int(lib().gp_batch_schedule_count())
+
+
+def gp_batch_schedule_name(i: int):
+    r = lib().gp_batch_schedule_name(int(i))
+    return r.decode() if r is not None else None
+
+
+def gp_batch_set_schedule(i: int):
+    _check(lib().gp_batch_set_schedule(int(i)), "gp_batch_set_schedule")
+
+
+def gp_batch_autotune(handles, r_cpu=None, tol=0.03, seeds=None, stream=None):
+    """Time every batch schedule on this batch, keep the fastest; returns (best, ms per schedule)."""
+    count, hs, rc, sd = _batch_args(handles, r_cpu, seeds)
+    k = gp_batch_schedule_count()
+    best = C.c_int32()
+    ms = (C.c_float * k)()
+    _check(lib().gp_batch_autotune(count, hs, rc, float(tol), sd, C.byref(best), ms, _stream(stream)),
+           "gp_batch_autotune")
+    return int(best.value), [float(ms[i]) for i in range(k)]
 
 
 def gp_launch_count() -> int:

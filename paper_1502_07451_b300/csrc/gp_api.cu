@@ -18,12 +18,13 @@
 #include "k_initial.cuh"
 #include "k_refine.cuh"
 #include "k_makespan.cuh"
+#include "k_batch.cuh"
 
 namespace gp {
 
 const char* const kFamilyName[F_COUNT] = {
     "validate", "transpose", "levels", "sym_merge", "match_pick", "match_confirm", "twohop", "cmap",
-    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc"};
+    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch"};
 
 // ------------------------------------------------------------------------------------------------
 // launch accounting and optional per-launch event timing
@@ -990,3 +991,5 @@ gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, cons
 
 // the no-allocation makespan variant (its scratch array must share this translation unit)
 #include "gp_noalloc.cu"
+// many graphs in one persistent launch
+#include "gp_batch.cu"

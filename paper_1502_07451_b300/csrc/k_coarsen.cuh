@@ -64,18 +64,49 @@ __device__ __forceinline__ unsigned group_mask(int G) {
   return (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
 }
 
-// One handshake round, picks: a group of G lanes per unmatched vertex.
+// Running best edge of one lane under the matching key.  Edge weights are compared first; the
+// tie-break hash is computed only when two offered edges have equal W (rare for summed weights).
+struct LazyKey {
+  int64_t W = -1;  // -1: nothing offered (weights are >= 0)
+  uint32_t u = 0;
+  bool hashed = false;
+  EdgeKey k;
+  __device__ __forceinline__ void offer(int64_t w, uint32_t uu, uint64_t seed, uint32_t v) {
+    if (w > W) {
+      W = w;
+      u = uu;
+      hashed = false;
+    } else if (w == W) {
+      if (!hashed) {
+        k = make_key(W, seed, v, u);
+        hashed = true;
+      }
+      const EdgeKey kn = make_key(w, seed, v, uu);
+      if (key_better(kn, k)) {
+        k = kn;
+        u = uu;
+      }
+    }
+  }
+  __device__ __forceinline__ EdgeKey key(uint64_t seed, uint32_t v) const {
+    if (W < 0) return key_none();
+    return hashed ? k : make_key(W, seed, v, u);
+  }
+};
+
+// One handshake round, picks: a group of G lanes per unmatched vertex.  `tid` / `stride`: the
+// calling thread and the number of threads sharing the level (grid or one CTA).  Returns, per
+// thread, whether it recorded a pick.
 template <int G>
-__global__ void __launch_bounds__(256)
-    k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const long long* __restrict__ maxw,
-                 const int32_t* __restrict__ mate, int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
+__device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, long long mC, long long mG,
+                           const int32_t* __restrict__ mate, int32_t* __restrict__ pick,
+                           uint8_t* __restrict__ alive, int64_t tid, int64_t stride) {
   __shared__ unsigned long long sacc[32];
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
   const unsigned gmask = group_mask(G);
-  const long long mC = maxw[0], mG = maxw[1];
   unsigned long long bytes = 0;
+  bool picked = false;
   for (int64_t v = group; v < g.n; v += ngroups) {
     if (sub == 0) bytes += 5;
     if (mate[v] != -1 || !alive[v]) continue;  // same v across the group: uniform
@@ -83,7 +114,7 @@ __global__ void __launch_bounds__(256)
     const int32_t d = g.deg[v];
     const int64_t cv = g.vC[v], gv = g.vG[v];
     const bool nocap = cv + mC <= capC && gv + mG <= capG;
-    EdgeKey best = key_none();
+    LazyKey lk;
     for (int32_t k = sub; k < d; k += G) {
       const int32_t u = g.adj[b + k];
       bytes += 8;
@@ -93,10 +124,9 @@ __global__ void __launch_bounds__(256)
         if (cv + g.vC[u] > capC || gv + g.vG[u] > capG) continue;
       }
       bytes += 8;
-      const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)u);
-      if (key_better(kk, best)) best = kk;
+      lk.offer(g.W[b + k], (uint32_t)u, seed, (uint32_t)v);
     }
-    best = group_best_key(best, gmask, G);
+    const EdgeKey best = group_best_key(lk.key(seed, (uint32_t)v), gmask, G);
     if (sub == 0) {
       bytes += 12 + 16 + 4;
       if (best.W < 0) {
@@ -104,10 +134,19 @@ __global__ void __launch_bounds__(256)
         alive[v] = 0;  // no eligible neighbour now means none later: neighbours only get matched
       } else {
         pick[v] = key_other(best, (uint32_t)v);
+        picked = true;
       }
     }
   }
   account(F_MATCH_PICK, bytes, sacc);
+  return picked;
+}
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const long long* __restrict__ maxw,
+                 const int32_t* __restrict__ mate, int32_t* __restrict__ pick, uint8_t* __restrict__ alive) {
+  match_pick<G>(g, capC, capG, seed, maxw[0], maxw[1], mate, pick, alive,
+                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick) {
@@ -120,12 +159,11 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
 
 // anchor of every unmatched vertex: its best neighbour under the matching key (no filters)
 template <int G>
-__global__ void __launch_bounds__(256)
-    k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
-             uint8_t* __restrict__ is_anchor) {
+__device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* __restrict__ mate,
+                             int32_t* __restrict__ anchor, uint8_t* __restrict__ is_anchor, int64_t tid,
+                             int64_t stride) {
   __shared__ unsigned long long sacc[32];
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
   const unsigned gmask = group_mask(G);
   unsigned long long bytes = 0;
@@ -139,13 +177,12 @@ __global__ void __launch_bounds__(256)
     }
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
-    EdgeKey best = key_none();
+    LazyKey lk;
     for (int32_t k = sub; k < d; k += G) {
-      const EdgeKey kk = make_key(g.W[b + k], seed, (uint32_t)v, (uint32_t)g.adj[b + k]);
-      if (key_better(kk, best)) best = kk;
+      lk.offer(g.W[b + k], (uint32_t)g.adj[b + k], seed, (uint32_t)v);
       bytes += 12;
     }
-    best = group_best_key(best, gmask, G);
+    const EdgeKey best = group_best_key(lk.key(seed, (uint32_t)v), gmask, G);
     if (sub == 0) {
       bytes += 20;
       if (best.W < 0) {
@@ -158,6 +195,13 @@ __global__ void __launch_bounds__(256)
     }
   }
   account(F_TWOHOP, bytes, sacc);
+}
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
+             uint8_t* __restrict__ is_anchor) {
+  match_anchor<G>(g, seed, mate, anchor, is_anchor, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                  (int64_t)gridDim.x * blockDim.x);
 }
 
 // Pairs the vertices anchored at h in ascending vertex order.  Sequentially: a vertex joins the
@@ -311,20 +355,16 @@ __device__ int32_t* warp_radix_keys(int32_t* A, int32_t* B, int k, int nbits, in
 }
 
 // Warp per anchor: gathers its anchored vertices (rows are in no particular order), sorts them and
-// pairs them.  Anchors with more than kSatCap of them go to a list for k_twohop_big.
-__global__ void __launch_bounds__(kTwohopWarps * 32)
-    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
-             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate, int32_t* __restrict__ big,
-             unsigned* big_cnt, int nbits) {
-  __shared__ int32_t sat[kTwohopWarps][2][kSatCap];
-  __shared__ int hist_all[kTwohopWarps][256];
-  __shared__ unsigned long long sacc[32];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+// pairs them.  Anchors with more than `cap` of them go to the list `big`.  `gw` / `nw`: this warp
+// and the number of warps sharing the level; S0 / S1 (cap keys each) and hist (256) are the warp's
+// shared-memory buffers.
+__device__ void twohop_warps(const LevelGraph& g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
+                             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate,
+                             int32_t* __restrict__ big, unsigned* big_cnt, int nbits, int64_t gw, int64_t nw,
+                             int32_t* S0, int32_t* S1, int* hist, int cap, unsigned long long& bytes) {
+  const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
-  int32_t* S = sat[wib][0];
-  const int64_t gw = (int64_t)blockIdx.x * kTwohopWarps + wib;
-  const int64_t nw = (int64_t)gridDim.x * kTwohopWarps;
-  unsigned long long bytes = 0;
+  int32_t* S = S0;
   for (int64_t hb = gw * 32; hb < g.n; hb += nw * 32) {
     unsigned am = __ballot_sync(0xffffffffu, hb + lane < g.n && is_anchor[hb + lane]);
     while (am) {
@@ -344,7 +384,7 @@ __global__ void __launch_bounds__(kTwohopWarps * 32)
           bytes += 8;
         }
         const unsigned m = __ballot_sync(0xffffffffu, flag);
-        if (k + __popc(m) > kSatCap) {
+        if (k + __popc(m) > cap) {
           over = true;
           break;
         }
@@ -364,12 +404,24 @@ __global__ void __launch_bounds__(kTwohopWarps * 32)
         S[lane] = x;
         __syncwarp();
       } else {
-        sorted = warp_radix_keys(S, sat[wib][1], k, nbits, hist_all[wib]);
+        sorted = warp_radix_keys(S, S1, k, nbits, hist);
       }
       pair_sorted(g, capC, capG, sorted, k, mate, bytes);
       __syncwarp();
     }
   }
+}
+__global__ void __launch_bounds__(kTwohopWarps * 32)
+    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
+             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate, int32_t* __restrict__ big,
+             unsigned* big_cnt, int nbits) {
+  __shared__ int32_t sat[kTwohopWarps][2][kSatCap];
+  __shared__ int hist_all[kTwohopWarps][256];
+  __shared__ unsigned long long sacc[32];
+  const int wib = threadIdx.x >> 5;
+  unsigned long long bytes = 0;
+  twohop_warps(g, capC, capG, anchor, is_anchor, mate, big, big_cnt, nbits, (int64_t)blockIdx.x * kTwohopWarps + wib,
+               (int64_t)gridDim.x * kTwohopWarps, sat[wib][0], sat[wib][1], hist_all[wib], kSatCap, bytes);
   account(F_TWOHOP, bytes, sacc);
 }
 
@@ -469,10 +521,10 @@ __global__ void k_rep_flags(int64_t n, const int32_t* __restrict__ mate, uint8_t
 
 // cmap holds the exclusive scan of the representative flags; complete it and set up the coarse
 // vertices: members, summed weights, raw row length.
-__global__ void k_cmap_fill(LevelGraph g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
-                            int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of,
-                            int64_t* __restrict__ cvC, int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+__device__ void cmap_fill(const LevelGraph& g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
+                          int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of, int64_t* __restrict__ cvC,
+                          int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen, int64_t tid, int64_t stride) {
+  for (int64_t v = tid; v < g.n; v += stride) {
     const int32_t u = mate[v];
     if (u < 0 || v < u) {
       const int32_t c = cmap[v];
@@ -485,6 +537,12 @@ __global__ void k_cmap_fill(LevelGraph g, const int32_t* __restrict__ mate, int3
       cmap[v] = cmap[u];
     }
   }
+}
+__global__ void k_cmap_fill(LevelGraph g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
+                            int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of,
+                            int64_t* __restrict__ cvC, int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen) {
+  cmap_fill(g, mate, cmap, rep_of, mate_of, cvC, cvG, rawlen, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+            (int64_t)gridDim.x * blockDim.x);
 }
 
 static inline unsigned grid_for(int64_t work, int per_block, int max_per_sm = 16) {

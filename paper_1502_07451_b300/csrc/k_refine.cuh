@@ -58,10 +58,14 @@ __device__ __forceinline__ u128 cand_key(long long gmax, long long gain, int32_t
   return ((u128)(unsigned long long)(gmax - gain) << idbits) | (u128)(uint32_t)id;
 }
 
-__global__ void k_ref_loads(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl) {
+// The round bodies below take the calling thread's index and the thread count of the range that
+// shares the work: the whole grid for the single-graph kernels, one CTA in the batch path (where
+// the control block lives in shared memory).
+__device__ void ref_loads(const LevelGraph& g, const uint8_t* __restrict__ part, Ctl* ctl, int64_t tid,
+                          int64_t stride) {
   __shared__ long long sh[32];
   long long c = 0, gg = 0;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t v = tid; v < g.n; v += stride) {
     if (part[v] == 0)
       c += g.vC[v];
     else
@@ -74,6 +78,9 @@ __global__ void k_ref_loads(LevelGraph g, const uint8_t* __restrict__ part, Ctl*
     if (gg) atomicAdd((unsigned long long*)&ctl->LG, (unsigned long long)gg);
   }
 }
+__global__ void k_ref_loads(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl) {
+  ref_loads(g, part, ctl, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
 
 __device__ __forceinline__ void reset_counters(CandCounters& c) {
   c.ncand = 0;
@@ -83,7 +90,7 @@ __device__ __forceinline__ void reset_counters(CandCounters& c) {
   c.gmin = LLONG_MAX;
 }
 
-__global__ void k_ref_begin(Ctl* ctl, int idbits) {
+__device__ void ref_begin(Ctl* ctl, int idbits) {  // one thread
   Ctl& c = *ctl;
   c.done = 0;
   c.streak = 0;
@@ -107,14 +114,14 @@ __global__ void k_ref_begin(Ctl* ctl, int idbits) {
     c.side_src = overC ? 0 : 1;
   }
 }
+__global__ void k_ref_begin(Ctl* ctl, int idbits) { ref_begin(ctl, idbits); }
 
 // gain of every vertex (a group of G lanes per row), once per level
 template <int G>
-__global__ void __launch_bounds__(256)
-    k_gain_all(LevelGraph g, const uint8_t* __restrict__ part, long long* __restrict__ gainv) {
+__device__ void gain_all(const LevelGraph& g, const uint8_t* __restrict__ part, long long* __restrict__ gainv,
+                         int64_t tid, int64_t stride) {
   __shared__ unsigned long long sacc[32];
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
   const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
   unsigned long long bytes = 0;
@@ -137,6 +144,11 @@ __global__ void __launch_bounds__(256)
   }
   account(F_GAIN, bytes, sacc);
 }
+template <int G>
+__global__ void __launch_bounds__(256)
+    k_gain_all(LevelGraph g, const uint8_t* __restrict__ part, long long* __restrict__ gainv) {
+  gain_all<G>(g, part, gainv, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
 
 __device__ __forceinline__ void push_cand(CandCounters* cc, const Cands& cand, int32_t v, long long gain,
                                           long long cdv, long long csv, unsigned long long& sum_cd,
@@ -155,8 +167,8 @@ __device__ __forceinline__ void push_cand(CandCounters* cc, const Cands& cand, i
 // Candidates of round r (-1 = balance): from the stored gains, except for the vertices the previous
 // round's moves made stale (stamp == prev_tag), whose gains are recomputed here by a warp each and
 // stored back.  Both parts write disjoint vertices.
-__global__ void __launch_bounds__(256)
-    k_ref_cands(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag, Cands cand) {
+__device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag,
+                          const Cands& cand, int64_t tid, int64_t stride) {
   __shared__ long long sh[32];
   __shared__ unsigned long long shu[32];
   __shared__ unsigned long long sacc[32];
@@ -176,8 +188,6 @@ __global__ void __launch_bounds__(256)
   const int64_t* csrc = src == 0 ? g.vC : g.vG;
   unsigned long long sum_cd = 0, sum_cs = 0, bytes = 0;
   long long gmax = LLONG_MIN, gmin = LLONG_MAX;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t v = tid; v < g.n; v += stride) {
     bytes += 1;
     if (part[v] != src) continue;
@@ -240,6 +250,11 @@ __global__ void __launch_bounds__(256)
     }
   }
   account(F_GAIN, bytes, sacc);
+}
+__global__ void __launch_bounds__(256)
+    k_ref_cands(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag, Cands cand) {
+  ref_cands(g, part, ctl, r, prev_tag, cand, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+            (int64_t)gridDim.x * blockDim.x);
 }
 
 // Among the candidates in key order, the first one at which the running weight exceeds T (T >= 0).
@@ -315,7 +330,7 @@ __device__ __forceinline__ int bits_of(unsigned long long x) {  // bits needed t
   return x == 0 ? 1 : 64 - __clzll((long long)x);
 }
 
-__global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, int64_t n, Cands cand) {
+__device__ void ref_select(Ctl* ctl, int r, const Cands& cand) {  // one block
   __shared__ unsigned long long hw[256], hc[256];
   __shared__ SelOut so;
   __shared__ int s_skip;
@@ -398,11 +413,12 @@ __global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, int64_t n,
     }
   }
 }
+__global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, Cands cand) { ref_select(ctl, r, cand); }
 
 // Moves the accepted candidates and stamps them and their neighbours as stale for the next round
 // (a warp per candidate; atomicExch on the stamp lists each stale vertex once).
-__global__ void __launch_bounds__(256)
-    k_ref_apply(Ctl* ctl, int r, LevelGraph g, uint8_t* __restrict__ part, int32_t tag, Cands cand) {
+__device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restrict__ part, int32_t tag,
+                          const Cands& cand, int64_t tid, int64_t stride) {
   __shared__ long long sh[32];
   __shared__ unsigned long long sacc[32];
   __shared__ int s_go;
@@ -429,8 +445,8 @@ __global__ void __launch_bounds__(256)
   int32_t* dl = cand.dirty[(r + 1) & 1];
   long long dC = 0, dG = 0;
   unsigned long long bytes = 0;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t gw = tid >> 5;
+  const int64_t nw = stride >> 5;
   for (int64_t i = gw; i < (int64_t)s_N; i += nw) {
     const int32_t v = cand.id[i];
     if (s_accept == 2 && !(cand_key(s_gmax, cand.gain[i], v, s_idbits) < thr)) continue;
@@ -462,6 +478,11 @@ __global__ void __launch_bounds__(256)
     if (dG) atomicAdd((unsigned long long*)&ctl->LG, (unsigned long long)dG);
   }
   account(F_APPLY, bytes, sacc);
+}
+__global__ void __launch_bounds__(256)
+    k_ref_apply(Ctl* ctl, int r, LevelGraph g, uint8_t* __restrict__ part, int32_t tag, Cands cand) {
+  ref_apply(ctl, r, g, part, tag, cand, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+            (int64_t)gridDim.x * blockDim.x);
 }
 
 // per-level record: rounds, moves, balanced, balance moves
@@ -523,7 +544,7 @@ void refine_level_run(const LevelGraph& g, uint8_t* part, Ctl* ctl, const Cands&
   int32_t prev = round_tag(level, -2);  // no stale vertices before the balance round
   for (int r = -1; r < kRefineRounds; r++) {
     GP_LAUNCH(F_GAIN, k_ref_cands, vgrid, 256, 0, s, g, part, ctl, r, prev, cand);
-    GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, r, n, cand);
+    GP_LAUNCH(F_SELECT, k_ref_select, 1, 1024, 0, s, ctl, r, cand);
     GP_LAUNCH(F_APPLY, k_ref_apply, agrid, 256, 0, s, ctl, r, g, part, round_tag(level, r), cand);
     prev = round_tag(level, r);
   }

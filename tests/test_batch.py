@@ -1,0 +1,187 @@
+"""The batched path: many graphs in one persistent launch, every result equal to the
+single-graph result and to the CPU oracle (bit-exact), for every schedule.
+
+Inputs are the mixed batch recipe (tiled Cholesky, tiled LU, layered random DAGs of
+log-uniform size), plus degenerate graphs.  All calls go through the C-ABI.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1502_07451_b300 as gp
+from paper_1502_07451_b300 import gen
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+RES_KEYS = ("cut", "load_cpu", "load_gpu", "bound_cpu", "bound_gpu", "feasible", "levels", "rounds", "coarsest_n")
+
+
+def dgraph(g):
+    return {k: (torch.from_numpy(np.ascontiguousarray(v)).cuda()
+                if isinstance(v, np.ndarray) and k in ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+                else v) for k, v in g.items()}
+
+
+def mixed(count, nmax, seed=0):
+    return [gen.build_from_spec(it) for it in gen.batch_spec(count, nmin=100, nmax=nmax, base_seed=seed)]
+
+
+def run_batch(graphs, r_cpu=None, seeds=None, tol=0.03, host_parts=False, makespans=True):
+    Gs = [gp.Graph(dgraph(g)) for g in graphs]
+    try:
+        if host_parts:
+            parts = [np.zeros(max(g["n"], 1), np.uint8) for g in graphs]
+        else:
+            parts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
+        res, ms = gp.gp_batch_partition([G.h for G in Gs], parts, r_cpu=r_cpu, tol=tol, seeds=seeds,
+                                        makespans=makespans)
+        out = [(p if host_parts else p.cpu().numpy())[: g["n"]].copy() for p, g in zip(parts, graphs)]
+        return out, res, ms
+    finally:
+        for G in Gs:
+            G.close()
+
+
+def check_oracle(graphs, parts, res, ms, r_cpu=None, seeds=None, tol=0.03):
+    for i, g in enumerate(graphs):
+        r = -1.0 if r_cpu is None else r_cpu[i]
+        s = 0 if seeds is None else seeds[i]
+        p_ref, res_ref = oracle.partition(g, r, tol, s)
+        assert np.array_equal(parts[i], p_ref[: g["n"]]), "graph %d split" % i
+        for k in RES_KEYS:
+            assert res[i][k] == res_ref[k], "graph %d %s: %d vs %d" % (i, k, res[i][k], res_ref[k])
+        if ms is not None:
+            assert ms[i] == oracle.makespan(g, p_ref), "graph %d makespan" % i
+
+
+def test_mixed_batch_matches_oracle():
+    graphs = mixed(40, 8000, seed=3)
+    parts, res, ms = run_batch(graphs)
+    check_oracle(graphs, parts, res, ms)
+
+
+def test_batch_per_graph_ratio_and_seed():
+    graphs = mixed(24, 4000, seed=11)
+    r_cpu = [-1.0 if i % 3 == 0 else (0.05 * (i % 19)) for i in range(len(graphs))]
+    seeds = [i * 7919 + 5 for i in range(len(graphs))]
+    parts, res, ms = run_batch(graphs, r_cpu=r_cpu, seeds=seeds, tol=0.05)
+    check_oracle(graphs, parts, res, ms, r_cpu=r_cpu, seeds=seeds, tol=0.05)
+
+
+def test_batch_host_buffers_and_no_makespan():
+    graphs = mixed(12, 3000, seed=5)
+    parts, res, ms = run_batch(graphs, host_parts=True, makespans=False)
+    assert ms is None
+    check_oracle(graphs, parts, res, None)
+
+
+def test_batch_degenerate_graphs():
+    graphs = [
+        gen.from_edges(0, [], [], [], []),
+        gen.from_edges(1, [], [7], [3], []),
+        gen.from_edges(2, [(0, 1)], [5, 5], [1, 1], [4]),
+        gen.cholesky(4),                        # 20 tasks: no coarsening at all
+        gen.two_input_dag(38, 3, extra=2),
+        gen.from_edges(1001, [(0, i) for i in range(1, 1001)], [10] * 1001, [5] * 1001, [1] * 1000),  # hub
+        gen.random_dag(300, 12000, 6),         # dense rows: the block-wide merge tiers
+        gen.layered(30, 200, 30000, 9),
+    ]
+    # r_cpu 0: all-GPU without trials; 1: everything must leave the GPU
+    r_cpu = [-1.0, -1.0, 0.0, 1.0, -1.0, -1.0, 0.3, -1.0]
+    parts, res, ms = run_batch(graphs, r_cpu=r_cpu)
+    check_oracle(graphs, parts, res, ms, r_cpu=r_cpu)
+
+
+def test_schedules_leave_results_unchanged():
+    graphs = mixed(30, 6000, seed=21)
+    ref = run_batch(graphs)
+    try:
+        for i in range(gp.gp_batch_schedule_count()):
+            gp.gp_batch_set_schedule(i)
+            parts, res, ms = run_batch(graphs)
+            for a, b in zip(parts, ref[0]):
+                assert np.array_equal(a, b), gp.gp_batch_schedule_name(i)
+            assert [{k: r[k] for k in RES_KEYS} for r in res] == [{k: r[k] for k in RES_KEYS} for r in ref[1]]
+            assert ms == ref[2]
+    finally:
+        gp.gp_batch_set_schedule(-1)
+    check_oracle(graphs, *ref)
+
+
+def test_autotune_picks_a_schedule():
+    graphs = mixed(16, 3000, seed=2)
+    Gs = [gp.Graph(dgraph(g)) for g in graphs]
+    try:
+        best, ms = gp.gp_batch_autotune([G.h for G in Gs])
+        assert 0 <= best < gp.gp_batch_schedule_count()
+        assert len(ms) == gp.gp_batch_schedule_count() and all(t > 0 for t in ms)
+        assert ms[best] == min(ms)
+    finally:
+        for G in Gs:
+            G.close()
+    parts, res, msp = run_batch(graphs)  # the tuned schedule gives the same results
+    check_oracle(graphs, parts, res, msp)
+
+
+def test_batch_equals_single_graph_path():
+    graphs = mixed(20, 12000, seed=8)
+    parts, res, ms = run_batch(graphs)
+    for i, g in enumerate(graphs):
+        with gp.Graph(dgraph(g)) as G:
+            p = torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda")
+            r = G.partition(p, -1.0, 0.03, 0)
+            assert np.array_equal(p.cpu().numpy()[: g["n"]], parts[i])
+            for k in RES_KEYS:
+                assert r[k] == res[i][k]
+            assert G.makespan(p[: g["n"]]) == ms[i]
+
+
+def test_deferred_graphs_keep_their_results():
+    """A workspace too small for the larger graphs: they are deferred to the single-graph path
+    inside the same call, with unchanged results."""
+    code = r'''
+import sys, json
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+import numpy as np, torch
+import paper_1502_07451_b300 as gp
+from paper_1502_07451_b300 import gen
+import oracle
+graphs = [gen.build_from_spec(it) for it in gen.batch_spec(10, nmin=200, nmax=5000, base_seed=4)]
+Gs = [gp.Graph({k: (torch.from_numpy(np.ascontiguousarray(v)).cuda() if isinstance(v, np.ndarray) and k in
+       ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost") else v) for k, v in g.items()}) for g in graphs]
+parts = [torch.zeros(g["n"], dtype=torch.uint8, device="cuda") for g in graphs]
+res, ms = gp.gp_batch_partition([G.h for G in Gs], parts, makespans=True)
+bad = 0
+for i, g in enumerate(graphs):
+    p_ref, r_ref = oracle.partition(g)
+    bad += int(not np.array_equal(parts[i].cpu().numpy(), p_ref))
+    bad += int(res[i]["cut"] != r_ref["cut"]) + int(ms[i] != oracle.makespan(g, p_ref))
+print(json.dumps({"bad": bad}))
+''' % (ROOT, os.path.join(ROOT, "tests"))
+    env = dict(os.environ, GP_BATCH_SLOT_LIMIT="600000")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    assert '"bad": 0' in out.stdout
+
+
+def test_batch_invalid_arguments():
+    g = gen.cholesky(5)
+    with gp.Graph(dgraph(g)) as G:
+        p = torch.zeros(g["n"], dtype=torch.uint8, device="cuda")
+        for kw in [dict(tol=-0.1), dict(tol=1.5), dict(r_cpu=[1.5]), dict(r_cpu=[float("nan")])]:
+            with pytest.raises(gp.GpError) as e:
+                gp.gp_batch_partition([G.h], [p], **kw)
+            assert e.value.status == gp.GP_ERR_INVALID
+        with pytest.raises(gp.GpError):
+            gp.gp_batch_partition([G.h], [None])
+    L = gp.lib()
+    assert L.gp_batch_partition(-1, None, None, 0.03, None, None, None, None, None) == gp.GP_ERR_INVALID
+    assert L.gp_batch_partition(0, None, None, 0.03, None, None, None, None, None) == gp.GP_OK
+    assert gp.lib().gp_batch_set_schedule(gp.gp_batch_schedule_count()) == gp.GP_ERR_INVALID
