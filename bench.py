@@ -6,7 +6,15 @@ gp_partition (coarsening, initial split, refinement, cut) and gp_makespan.
 Workload: layered random DAG, 1,000 layers x 1,000 vertices, 8M edges,
 lognormal CPU times, GPU = CPU / U(2, 40), transfer U{1..10,000} ns, seed 0.
 
+The line also carries a "batch" object: 4,096 DAGs of log-uniform size
+100..50,000 (tiled Cholesky, tiled LU, layered) partitioned by
+gp_batch_partition (one persistent launch replayed from a captured CUDA graph)
+against the plain path (gp_partition + gp_makespan per graph, in a loop),
+with the graphs resident in HBM.  --workload batch makes that the main line
+(metric graphs/s).
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload layered1m|batch] [--no-batch]
 
 Under torchrun (N > 1) every rank runs an independent replica (the single-DAG
 path does not shard); value = edges processed by all ranks / max rank time.
@@ -28,6 +36,39 @@ sys.path.insert(0, ROOT)
 METRIC = "dag_edges_partitioned_per_sec"
 UNIT = "edges/s"
 WORKLOAD = "layered DAG 1,000 layers x 1,000 vertices, 8,000,000 edges, seed 0"
+BATCH_METRIC = "dag_graphs_partitioned_per_sec"
+BATCH_UNIT = "graphs/s"
+BATCH_COUNT = 4096
+BATCH_WORKLOAD = ("4,096 DAGs, log-uniform 100..50,000 vertices, kinds in turn tiled Cholesky (T 4..40), "
+                  "tiled LU, layered (width ~sqrt(n), 8 edges per vertex to the next 1-4 layers); base seed 0")
+
+
+def _build_chunk(chunk):
+    from paper_1502_07451_b300 import gen
+    return [gen.build_from_spec(it) for it in chunk]
+
+
+class BatchGen:
+    """Builds the batch's graphs in spawned worker processes (started before any CUDA call)."""
+
+    def __init__(self, count=BATCH_COUNT):
+        import multiprocessing as mp
+        from paper_1502_07451_b300 import gen
+        self.count = count
+        self.spec = gen.batch_spec(count)
+        self.nproc = max(1, min(32, os.cpu_count() or 4))
+        self.pool = mp.get_context("spawn").Pool(self.nproc)
+        self.chunks = [self.spec[i::self.nproc] for i in range(self.nproc)]
+        self.res = self.pool.map_async(_build_chunk, self.chunks)
+
+    def graphs(self):
+        out = [None] * self.count
+        for i, part in enumerate(self.res.get()):
+            for j, g in enumerate(part):
+                out[i + j * self.nproc] = g
+        self.pool.close()
+        self.pool.join()
+        return out
 
 
 def peaks():
@@ -110,10 +151,50 @@ def oracle_step(g):
     return time.perf_counter() - t0, part, res, ms
 
 
+def oracle_batch_sample(graphs, budget_s=12.0):
+    """The oracle over the batch's graphs in order until about budget_s seconds of CPU work."""
+    import oracle
+    t0 = time.perf_counter()
+    k = 0
+    for g in graphs:
+        part, _ = oracle.partition(g)
+        oracle.makespan(g, part)
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return k, time.perf_counter() - t0
+
+
+def run_reference_batch(args, rank, world):
+    if rank != 0:
+        return
+    bg = BatchGen(256)
+    graphs = bg.graphs()
+    oracle_batch_sample(graphs[:2], 1e9)
+    tot, done = 0.0, 0
+    for _ in range(args.steps):
+        k, dt = oracle_batch_sample(graphs, 20.0 / max(args.steps, 1))
+        tot += dt
+        done += k
+    value = done / tot
+    desc = "the first graphs of the batch recipe in order (%d graphs over %d steps), oracle partition + makespan" % (
+        done, args.steps)
+    line = {"metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "sample": desc}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": BATCH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, timed on a bounded sample of the workload (first 100 layers)."""
     from paper_1502_07451_b300 import gen
     if rank != 0:
+        return
+    if args.workload == "batch":
+        run_reference_batch(args, rank, world)
         return
     sample = gen.layered(100, 1000, 800_000, 0)
     for _ in range(args.warmup):
@@ -140,12 +221,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="layered1m", choices=["layered1m", "batch"])
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered1m line")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    # the batch's graphs are built by spawned workers while the GPU part runs
+    bgen = BatchGen() if (args.workload == "batch" or (not args.no_batch and world == 1)) else None
+    if args.workload == "batch":
+        run_batch_line(args, rank, world, local_rank, bgen)
         return
 
     import torch
@@ -272,6 +360,10 @@ def main():
                "sample": "the full workload, one partition + makespan (%.1f s)" % dt}
         bit_exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == res["cut"] and oms == ms)
 
+    batch = None
+    if bgen is not None:
+        batch = bench_batch(bgen.graphs(), K, W, stream, flush, with_cpu=not args.no_cpu_baseline)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -293,9 +385,155 @@ def main():
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if batch:
+        line["batch"] = batch
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
+    """gp_batch_partition over the batch (graphs resident in HBM) against the plain path in a loop.
+
+    Returns the measurements as a dict (graphs/s, edges/s, the plain loop, e2e with host buffers,
+    the batch kernel's achieved bandwidth, the oracle on a bounded sample)."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    count = len(graphs)
+    m_tot = int(sum(g["m"] for g in graphs))
+    n_tot = int(sum(g["n"] for g in graphs))
+    dgs = [{k: torch.from_numpy(np.ascontiguousarray(g[k])).cuda() for k in keys} for g in graphs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs = [gp.gp_graph_create(g["n"], g["m"], *[d[k] for k in keys], stream=stream) for g, d in zip(graphs, dgs)]
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    parts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
+    best, sched_ms = gp.gp_batch_autotune(hs, stream=stream)
+    for _ in range(W):
+        res, mks = gp.gp_batch_partition(hs, parts, makespans=True, stream=stream)
+    torch.cuda.synchronize()
+    launches0 = gp.gp_launch_count()
+    tot_ms = 0.0
+    kern_ms = 0.0
+    for _ in range(K):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, mks = gp.gp_batch_partition(hs, parts, makespans=True, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        tot_ms += a.elapsed_time(b)
+        kern_ms += res[0]["ms"][0]
+    launches = gp.gp_launch_count() - launches0
+    # achieved bandwidth of the persistent kernel: algorithmic bytes of its steps / its time
+    gp.gp_prof_reset()
+    gp.gp_prof_enable(True)
+    flush.fill_(1)
+    gp.gp_batch_partition(hs, parts, makespans=True, stream=stream)
+    torch.cuda.synchronize()
+    gp.gp_prof_enable(False)
+    fams = gp.kernel_families()
+    prof = {f: gp.gp_prof_read(i) for i, f in enumerate(fams)}
+    gp.gp_prof_reset()
+    alg = sum(p["alg_bytes"] for p in prof.values())
+    bms = prof["batch"]["total_ms"]
+    hbm_peak, peak_kind = peaks()
+    # the plain path, one graph after another (same handles, same outputs)
+    p2 = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = []
+    for i, h in enumerate(hs):
+        r = gp.gp_partition(h, -1.0, 0.03, 0, p2[i], stream)
+        plain.append((r["cut"], gp.gp_makespan(h, p2[i][: graphs[i]["n"]], None, stream) if graphs[i]["n"] else 0))
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    same = all(torch.equal(a, b) for a, b in zip(parts, p2)) and all(
+        plain[i] == (res[i]["cut"], mks[i]) for i in range(count))
+    # end to end: create from pinned host arrays, partition into pinned host buffers, destroy
+    hgs = [{k: torch.from_numpy(np.ascontiguousarray(g[k])).pin_memory() for k in keys} for g in graphs]
+    hparts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8).pin_memory() for g in graphs]
+    h2d = sum(int(t.numel() * t.element_size()) for d in hgs for t in d.values())
+    d2h = n_tot + count * 56  # splits + the per-graph result records
+
+    def e2e_step():
+        hh = [gp.gp_graph_create(g["n"], g["m"], *[d[k] for k in keys], stream=stream) for g, d in zip(graphs, hgs)]
+        gp.gp_batch_partition(hh, hparts, makespans=True, stream=stream)
+        for h in hh:
+            gp.gp_graph_destroy(h)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ke = max(1, min(K, 3))
+    for _ in range(ke):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_ok = all(torch.equal(a.cpu(), b) for a, b in zip(parts, hparts))
+    cpu = None
+    if with_cpu:
+        k, dt = oracle_batch_sample(graphs, 12.0)
+        cpu = {"value": k / dt, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
+               "sample": "the first %d graphs of the batch in order, oracle partition + makespan (%.1f s)" % (k, dt)}
+    for h in hs:
+        gp.gp_graph_destroy(h)
+    out = {
+        "metric": BATCH_METRIC, "unit": BATCH_UNIT, "workload": BATCH_WORKLOAD, "graphs": count,
+        "vertices": n_tot, "edges": m_tot,
+        "value": K * count / (tot_ms / 1e3), "edges_per_sec": K * m_tot / (tot_ms / 1e3),
+        "ms_per_step": tot_ms / K, "kernel_ms_per_step": kern_ms / K, "steps": K, "warmup": W,
+        "step": "gp_batch_partition(4,096 resident handles, makespans on), one persistent launch",
+        "schedule": gp.gp_batch_schedule_name(best),
+        "autotune_ms": {gp.gp_batch_schedule_name(i): round(t, 2) for i, t in enumerate(sched_ms)},
+        "plain_graphs_per_sec": count / plain_s, "plain_step": "gp_partition + gp_makespan per graph",
+        "speedup_vs_plain": (K * count / (tot_ms / 1e3)) / (count / plain_s),
+        "results_equal_plain": bool(same), "gpu_launches": int(launches),
+        "create_s": create_s,
+        "e2e": {"value": count / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "step": "gp_graph_create from pinned host CSR for every graph + gp_batch_partition into pinned "
+                        "host buffers + destroy", "matches_device": bool(e2e_ok)},
+        "roofline": {"bound": "hbm", "kernel": "k_batch (persistent)", "achieved": alg / (bms * 1e-3) / 1e9,
+                     "peak": hbm_peak, "unit": "GB/s", "frac": alg / (bms * 1e-3) / 1e9 / hbm_peak,
+                     "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg, "launch_ms": bms},
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    return out
+
+
+def run_batch_line(args, rank, world, local_rank, bgen):
+    """--workload batch: the batch as the main line (graphs/s)."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    torch.cuda.set_device(local_rank)
+    gp.lib()
+    W = max(3, args.warmup)
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+    graphs = bgen.graphs()
+    sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    b = bench_batch(graphs, K, W, stream, flush, with_cpu=not args.no_cpu_baseline and world == 1)
+    clocks = sampler.stop() if sampler else None
+    if rank != 0:
+        return
+    line = {"metric": BATCH_METRIC, "value": world * b["value"], "unit": BATCH_UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "step": b["step"], "l2": "flushed between timed steps (256 MB)",
+                       "edges_per_sec": b["edges_per_sec"], "plain_graphs_per_sec": b["plain_graphs_per_sec"],
+                       "speedup_vs_plain": b["speedup_vs_plain"], "schedule": b["schedule"],
+                       "autotune_ms": b["autotune_ms"], "results_equal_plain": b["results_equal_plain"],
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "e2e": b["e2e"], "gpu_launches": b["gpu_launches"], "roofline": b["roofline"], "clocks": clocks}
+    if "cpu_baseline" in b:
+        line["cpu_baseline"] = b["cpu_baseline"]
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -22,6 +22,7 @@ DAGs) or from seeded distributions (layered random DAGs).
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -442,12 +443,17 @@ def batch_spec(count: int = 4096, nmin: int = 100, nmax: int = 50000, base_seed:
     return spec
 
 
+@functools.lru_cache(maxsize=None)
+def _tiled(kind: str, T: int):
+    return cholesky(T) if kind == "cholesky" else lu(T)
+
+
 def build_from_spec(item):
+    """The graph of one batch item.  Tiled Cholesky / LU graphs depend on T only and are built
+    once per T (the returned arrays are shared: treat them as read-only)."""
     kind, p, seed = item
-    if kind == "cholesky":
-        return cholesky(p)
-    if kind == "lu":
-        return lu(p)
+    if kind in ("cholesky", "lu"):
+        return _tiled(kind, p)
     layers, width = p
     n = layers * width
     cap = 0
