@@ -263,6 +263,15 @@ GP_API gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* ad
                          const int64_t* vC, const int64_t* vG, int64_t bound_cpu, int64_t bound_gpu,
                          uint8_t* part, int64_t* stats, void* stream);
 
+/* One layer product of the learned proposal's message-passing network (the paper has no network:
+ * this is a project addition), on the 5th-generation tensor cores: C[M x N] = A[M x K] . B[K x N]
+ * with BF16 inputs and FP32 accumulation, (N, K) in {(64, 192), (192, 64), (64, 64)}.
+ *   A  BF16 [M x K] row-major, DEVICE;  B  BF16 [K x N] row-major, DEVICE;  C  FP32 [M x N], DEVICE.
+ * Errors: GP_ERR_INVALID (shape, host pointers), GP_ERR_TIMEOUT (a tensor-core wait expired; the
+ * kernel released its tensor memory and returned), GP_ERR_OOM, GP_ERR_CUDA. */
+GP_API gp_status gp_step_mma_bf16(int64_t M, int32_t N, int32_t K, const void* A, const void* B, float* C,
+                                  void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation.
  * gp_launch_count: kernels launched by this library since load (all threads).

@@ -98,6 +98,7 @@ def lib():
                 "gp_batch_partition": [_I32, _P, _P, _D, _P, _P, _P, _P, _P],
                 "gp_batch_set_schedule": [_I32],
                 "gp_batch_autotune": [_I32, _P, _P, _D, _P, _P, _P, _P],
+                "gp_step_mma_bf16": [_I64, _I32, _I32, _P, _P, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -337,6 +338,15 @@ def gp_batch_autotune(handles, r_cpu=None, tol=0.03, seeds=None, stream=None):
     _check(lib().gp_batch_autotune(count, hs, rc, float(tol), sd, C.byref(best), ms, _stream(stream)),
            "gp_batch_autotune")
     return int(best.value), [float(ms[i]) for i in range(k)]
+
+
+def gp_step_mma_bf16(A, B, C, stream=None):
+    """C = A . B on the tensor cores (BF16 in, FP32 accumulate); device tensors, (N, K) in
+    {(64, 192), (192, 64), (64, 64)}."""
+    M, K = A.shape
+    N = B.shape[1]
+    _check(lib().gp_step_mma_bf16(int(M), int(N), int(K), _ptr(A)[0], _ptr(B)[0], _ptr(C)[0], _stream(stream)),
+           "gp_step_mma_bf16")
 
 
 def gp_launch_count() -> int:

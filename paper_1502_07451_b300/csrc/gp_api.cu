@@ -19,12 +19,13 @@
 #include "k_refine.cuh"
 #include "k_makespan.cuh"
 #include "k_batch.cuh"
+#include "k_umma.cuh"
 
 namespace gp {
 
 const char* const kFamilyName[F_COUNT] = {
     "validate", "transpose", "levels", "sym_merge", "match_pick", "match_confirm", "twohop", "cmap",
-    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch"};
+    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch", "mpnn", "propose"};
 
 // ------------------------------------------------------------------------------------------------
 // launch accounting and optional per-launch event timing
@@ -993,3 +994,5 @@ gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, cons
 #include "gp_noalloc.cu"
 // many graphs in one persistent launch
 #include "gp_batch.cu"
+// the learned proposal (message-passing network on the tensor cores)
+#include "gp_mpnn.cu"

@@ -1,0 +1,38 @@
+"""The tensor-core GEMM of the learned proposal (tcgen05, BF16 inputs, FP32 accumulation in tensor
+memory) against a plain FP32 product of the same BF16 values.
+
+Products of BF16 values are exact in FP32, so the only difference is the summation order:
+the bound is K * 2^-23 * sum |a||b| per entry (FP32 accumulation)."""
+import numpy as np
+import pytest
+
+import paper_1502_07451_b300 as gp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 192), (1000, 64, 192), (77, 192, 64), (4097, 192, 64),
+                                   (129, 64, 64), (1, 64, 192), (300000, 64, 192)])
+def test_mma_bf16_matches_fp32_reference(M, N, K):
+    g = torch.Generator(device="cpu").manual_seed(M * 131 + N * 7 + K)
+    A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B = torch.randn(K, N, generator=g).to(torch.bfloat16).cuda()
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    gp.gp_step_mma_bf16(A, B, C)
+    ref = A.double() @ B.double()
+    bound = K * 2.0 ** -22 * (A.double().abs() @ B.double().abs()) + 1e-30
+    err = (C.double() - ref).abs()
+    assert torch.isfinite(C).all()
+    assert (err <= bound).all(), float((err / bound).max())
+
+
+def test_mma_rejects_bad_shapes():
+    A = torch.zeros(8, 48, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(48, 64, dtype=torch.bfloat16, device="cuda")
+    C = torch.zeros(8, 64, dtype=torch.float32, device="cuda")
+    with pytest.raises(gp.GpError) as e:
+        gp.gp_step_mma_bf16(A, B, C)
+    assert e.value.status == gp.GP_ERR_INVALID
+    with pytest.raises(gp.GpError):
+        gp.gp_step_mma_bf16(A.cpu(), B.cpu(), C.cpu())
