@@ -273,6 +273,52 @@ GP_API gp_status gp_step_mma_bf16(int64_t M, int32_t N, int32_t K, const void* A
                                   void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Learned proposal (a project addition; the paper's initial split comes from METIS, Sec. III.A).
+ * A 3-layer message-passing network (hidden 64) scores every vertex; its logits propose the
+ * initial split, and the exact refinement of gp_partition (balance round + gain rounds) runs on
+ * level 0 only ("flat mode").  The integer results are exact given the logits.
+ *
+ * Network: x_v = [log1p(cpu)/16, log1p(gpu)/16, log1p(indeg)/4, log1p(outdeg)/4,
+ * level/max(1, levels-1)]; h0 = relu(x W_in + b_in); for l = 1..3,
+ * h_l = relu([h | sum_{u->v} e h_u / max(1, indeg) | sum_{v->u} e h_u / max(1, outdeg)] W_l + b_l)
+ * with e = log1p(transfer cost)/16 per directed entry; logit = h3 . w_o + b_o.  The layer products
+ * run on the tensor cores in BF16 with FP32 accumulation; neighbour sums are order-independent
+ * (fixed point), so outputs are deterministic.  Loss: mean binary cross-entropy with the target
+ * "the plain method put the vertex on the CPU".  Parameters: GP_MPNN_PARAMS FP32 values in the
+ * order W_in(5x64), b_in, W1(192x64), b1, W2, b2, W3, b3, w_o(64), b_o (row-major).
+ * ------------------------------------------------------------------------------------------- */
+typedef struct gp_model gp_model;
+#define GP_MPNN_PARAMS 37505
+
+/* New network on the current device, He-normal weights drawn from splitmix64(seed). */
+GP_API gp_status gp_model_create(uint64_t seed, gp_model** out);
+GP_API gp_status gp_model_destroy(gp_model* m);
+GP_API int64_t gp_model_param_count(void);
+/* FP32 parameters to / from host memory (GP_MPNN_PARAMS floats); set resets the optimiser. */
+GP_API gp_status gp_model_get_params(const gp_model* m, float* params);
+GP_API gp_status gp_model_set_params(gp_model* m, const float* params);
+/* Checkpoint: parameters, Adam moments and step (a private binary format with a magic header). */
+GP_API gp_status gp_model_save(const gp_model* m, const char* path);
+GP_API gp_status gp_model_load(const char* path, gp_model** out);
+/* logits_out: float[n], device or host. */
+GP_API gp_status gp_model_forward(const gp_model* m, const gp_graph* g, float* logits_out, void* stream);
+/* Gradient of the mean loss on one graph: labels uint8[n] (0 = CPU side, as gp_partition writes it;
+ * device or host); grad_out host float[GP_MPNN_PARAMS]; *loss_out the mean loss (may be NULL). */
+GP_API gp_status gp_model_grad(gp_model* m, const gp_graph* g, const uint8_t* labels, float* grad_out,
+                               double* loss_out, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) on one graph's gradient. */
+GP_API gp_status gp_model_train_step(gp_model* m, const gp_graph* g, const uint8_t* labels, float lr,
+                                     double* loss_out, void* stream);
+/* The learned path: logits from `logits` (float[n], device or host) when not NULL, else from the
+ * network m; vertices ordered by (logit desc, id asc) under the total order of the float bits (a
+ * NaN logit is GP_ERR_INVALID); the first k = min(longest prefix whose CPU load fits B_C, shortest
+ * prefix after which the GPU load fits B_G) go to the CPU; then the refinement of level 0.  Bounds as
+ * gp_partition (Eq. (1)-(2) with tol, or the given ratio).  res: levels = 0, coarsest_n = n,
+ * ms[0..2] = network, proposal, refinement + cut (when profiling is on). */
+GP_API gp_status gp_partition_learned(gp_graph* g, const gp_model* m, const float* logits, double r_cpu,
+                                      double tol, uint8_t* part_out, gp_result* res, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Instrumentation.
  * gp_launch_count: kernels launched by this library since load (all threads).
  * gp_prof_enable(1): record CUDA events around every launch of each kernel family (on the

@@ -112,6 +112,9 @@ def lib():
             L.og_cut.argtypes = [_I64, _P, _P, _P, _P, _P]
             L.og_levels.argtypes = [_I64, _I64, _P, _P, _P, _P]
             L.og_makespan.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.og_propose.argtypes = [_I64, _P, _P, _P, _I64, _I64, _P, _P]
+            L.og_partition_learned.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
+                                               _P, _P]
             _lib = L
     return _lib
 
@@ -271,6 +274,34 @@ def partition(g, r_cpu: float = -1.0, tol: float = 0.03, seed: int = 0, trace: b
                               _p(part), C.byref(res), C.byref(tr) if trace else None), "og_partition")
     if trace:
         return part[:n], res.as_dict(), tr.as_dict()
+    return part[:n], res.as_dict()
+
+
+def propose(logits, vC, vG, bound_cpu, bound_gpu):
+    """Learned proposal: vertices by (logit desc, id asc) under the total order of the float bits;
+    the first k = min(kC, kG) go to the CPU.  Returns (part, k)."""
+    lg = _c(logits, np.float32)
+    n = lg.shape[0]
+    vC = _c(vC, np.int64)
+    vG = _c(vG, np.int64)
+    part = np.zeros(max(n, 1), np.uint8)
+    k = C.c_int64()
+    _check(lib().og_propose(n, _p(lg), _p(vC), _p(vG), int(bound_cpu), int(bound_gpu), _p(part), C.byref(k)),
+           "og_propose")
+    return part[:n], int(k.value)
+
+
+def partition_learned(g, logits, r_cpu: float = -1.0, tol: float = 0.03):
+    """The learned path from given logits: proposal, then refinement at level 0 only."""
+    off, cols, w, cc, cg = _graph_arrays(g)
+    n = g["n"]
+    lg = _c(logits, np.float32)
+    if lg.shape[0] == 0:
+        lg = np.zeros(1, np.float32)
+    part = np.zeros(max(n, 1), np.uint8)
+    res = Result()
+    _check(lib().og_partition_learned(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), _p(lg), r_cpu, tol,
+                                      _p(part), C.byref(res)), "og_partition_learned")
     return part[:n], res.as_dict()
 
 

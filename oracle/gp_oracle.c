@@ -980,3 +980,130 @@ int og_makespan(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, c
   free(queue);
   return OG_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned proposal: order, then split.                                       */
+/*                                                                           */
+/* A logit's sort key is its IEEE-754 bit pattern mapped to an unsigned      */
+/* integer that increases with the float's total order (negative values:     */
+/* all bits flipped; others: sign bit set).  Vertices are visited by         */
+/* decreasing key, smaller id first on equal keys; visiting one moves it      */
+/* from the GPU side to the CPU side.  k = min(kC, kG) with kC the largest    */
+/* prefix length whose CPU load stays within B_C and kG the smallest prefix   */
+/* length whose remaining GPU load is within B_G.                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t key;
+  int32_t id;
+} og_lkey;
+
+static uint32_t og_float_key(float f) {
+  uint32_t b;
+  memcpy(&b, &f, sizeof(b));
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+static int og_cmp_lkey(const void* a, const void* b) {
+  const og_lkey* x = (const og_lkey*)a;
+  const og_lkey* y = (const og_lkey*)b;
+  if (x->key != y->key) return x->key > y->key ? -1 : 1; /* larger logit first */
+  return (x->id > y->id) - (x->id < y->id);
+}
+
+int og_propose(int64_t n, const float* logits, const int64_t* vC, const int64_t* vG, int64_t BC,
+               int64_t BG, uint8_t* part, int64_t* k_out) {
+  for (int64_t v = 0; v < n; v++)
+    if (isnan(logits[v])) return OG_ERR_INVALID;
+  og_lkey* order = (og_lkey*)malloc((size_t)(n > 0 ? n : 1) * sizeof(og_lkey));
+  if (!order) return OG_ERR_OOM;
+  int64_t SG = 0;
+  for (int64_t v = 0; v < n; v++) {
+    order[v].key = og_float_key(logits[v]);
+    order[v].id = (int32_t)v;
+    SG += vG[v];
+  }
+  qsort(order, (size_t)n, sizeof(og_lkey), og_cmp_lkey);
+  /* kC: largest k with sum of the first k CPU costs <= B_C */
+  int64_t kC = 0, LC = 0;
+  while (kC < n && LC + vC[order[kC].id] <= BC) {
+    LC += vC[order[kC].id];
+    kC++;
+  }
+  /* kG: smallest k with SG - sum of the first k GPU costs <= B_G */
+  int64_t kG = 0, LG = SG;
+  while (kG < n && LG > BG) {
+    LG -= vG[order[kG].id];
+    kG++;
+  }
+  const int64_t k = kC < kG ? kC : kG;
+  for (int64_t v = 0; v < n; v++) part[v] = 1;
+  for (int64_t i = 0; i < k; i++) part[order[i].id] = 0;
+  if (k_out) *k_out = k;
+  free(order);
+  return OG_OK;
+}
+
+int og_partition_learned(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                         const int32_t* cC, const int32_t* cG, const float* logits, double r_cpu,
+                         double tol, uint8_t* part, og_result* res) {
+  int st = og_validate(n, m, off, cols, w, cC, cG);
+  if (st != OG_OK) return st;
+  int64_t SC = 0, SG = 0;
+  for (int64_t v = 0; v < n; v++) {
+    SC += cC[v];
+    SG += cG[v];
+  }
+  int64_t BC, BG;
+  st = og_bounds(SC, SG, r_cpu, tol, &BC, &BG);
+  if (st != OG_OK) return st;
+  memset(res, 0, sizeof(*res));
+  res->bound_cpu = BC;
+  res->bound_gpu = BG;
+  if (n == 0) {
+    res->feasible = 1;
+    return OG_OK;
+  }
+  int64_t* uoff = (int64_t*)malloc((size_t)(n + 1) * sizeof(int64_t));
+  int32_t* uadj = (int32_t*)malloc((size_t)(2 * m + 1) * sizeof(int32_t));
+  int64_t* uW = (int64_t*)malloc((size_t)(2 * m + 1) * sizeof(int64_t));
+  int64_t* vC = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  int64_t* vG = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  int rc = OG_ERR_OOM;
+  if (!uoff || !uadj || !uW || !vC || !vG) goto done;
+  for (int64_t v = 0; v < n; v++) {
+    vC[v] = cC[v];
+    vG[v] = cG[v];
+  }
+  int64_t a = 0;
+  st = og_symmetrize(n, m, off, cols, w, uoff, uadj, uW, &a);
+  if (st != OG_OK) {
+    rc = st;
+    goto done;
+  }
+  st = og_propose(n, logits, vC, vG, BC, BG, part, NULL);
+  if (st != OG_OK) {
+    rc = st;
+    goto done;
+  }
+  og_refine_stats rs;
+  st = og_refine(n, uoff, uadj, uW, vC, vG, BC, BG, part, &rs);
+  if (st != OG_OK) {
+    rc = st;
+    goto done;
+  }
+  og_cut(n, off, cols, w, part, &res->cut);
+  res->load_cpu = rs.load_cpu;
+  res->load_gpu = rs.load_gpu;
+  res->feasible = (rs.load_cpu <= BC && rs.load_gpu <= BG);
+  res->levels = 0;
+  res->rounds = rs.rounds;
+  res->coarsest_n = (int32_t)n;
+  rc = OG_OK;
+done:
+  free(uoff);
+  free(uadj);
+  free(uW);
+  free(vC);
+  free(vG);
+  return rc;
+}

@@ -118,6 +118,18 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
 int og_cut(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* w,
            const uint8_t* part, int64_t* cut);
 
+/* Learned proposal (a project addition; the paper has none): order the vertices by (logit desc,
+ * id asc), logits compared as the total order of their IEEE-754 bits (NaN rejected); the first k
+ * go to the CPU, k = min(longest prefix with CPU load <= B_C, shortest prefix with GPU load <= B_G). */
+int og_propose(int64_t n, const float* logits, const int64_t* vC, const int64_t* vG, int64_t bound_cpu,
+               int64_t bound_gpu, uint8_t* part, int64_t* k_out);
+
+/* The learned path: bounds, symmetrised level 0, proposal from the logits, refinement at level 0
+ * only (flat mode), cut.  res->levels = 0, res->coarsest_n = n. */
+int og_partition_learned(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                         const int32_t* cpu_cost, const int32_t* gpu_cost, const float* logits,
+                         double r_cpu, double tol, uint8_t* part, og_result* res);
+
 int og_levels(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, int32_t* level,
               int32_t* nlevels);
 

@@ -99,6 +99,16 @@ def lib():
                 "gp_batch_set_schedule": [_I32],
                 "gp_batch_autotune": [_I32, _P, _P, _D, _P, _P, _P, _P],
                 "gp_step_mma_bf16": [_I64, _I32, _I32, _P, _P, _P, _P],
+                "gp_model_create": [_U64, C.POINTER(_P)],
+                "gp_model_destroy": [_P],
+                "gp_model_get_params": [_P, _P],
+                "gp_model_set_params": [_P, _P],
+                "gp_model_save": [_P, C.c_char_p],
+                "gp_model_load": [C.c_char_p, C.POINTER(_P)],
+                "gp_model_forward": [_P, _P, _P, _P],
+                "gp_model_grad": [_P, _P, _P, _P, _P, _P],
+                "gp_model_train_step": [_P, _P, _P, C.c_float, _P, _P],
+                "gp_partition_learned": [_P, _P, _P, _D, _D, _P, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -110,6 +120,8 @@ def lib():
             L.gp_kernel_name.restype = C.c_char_p
             L.gp_launch_count.argtypes = []
             L.gp_launch_count.restype = C.c_int64
+            L.gp_model_param_count.argtypes = []
+            L.gp_model_param_count.restype = C.c_int64
             L.gp_batch_schedule_count.argtypes = []
             L.gp_batch_schedule_count.restype = C.c_int32
             L.gp_batch_schedule_name.argtypes = [_I32]
@@ -347,6 +359,68 @@ def gp_step_mma_bf16(A, B, C, stream=None):
     N = B.shape[1]
     _check(lib().gp_step_mma_bf16(int(M), int(N), int(K), _ptr(A)[0], _ptr(B)[0], _ptr(C)[0], _stream(stream)),
            "gp_step_mma_bf16")
+
+
+MPNN_PARAMS = 37505
+
+
+def gp_model_create(seed=0):
+    h = _P()
+    _check(lib().gp_model_create(int(seed), C.byref(h)), "gp_model_create")
+    return h
+
+
+def gp_model_destroy(m):
+    _check(lib().gp_model_destroy(m), "gp_model_destroy")
+
+
+def gp_model_get_params(m):
+    out = np.zeros(MPNN_PARAMS, np.float32)
+    _check(lib().gp_model_get_params(m, out.ctypes.data), "gp_model_get_params")
+    return out
+
+
+def gp_model_set_params(m, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    if p.shape != (MPNN_PARAMS,):
+        raise ValueError("expected %d parameters" % MPNN_PARAMS)
+    _check(lib().gp_model_set_params(m, p.ctypes.data), "gp_model_set_params")
+
+
+def gp_model_save(m, path):
+    _check(lib().gp_model_save(m, str(path).encode()), "gp_model_save")
+
+
+def gp_model_load(path):
+    h = _P()
+    _check(lib().gp_model_load(str(path).encode(), C.byref(h)), "gp_model_load")
+    return h
+
+
+def gp_model_forward(m, g, logits_out, stream=None):
+    _check(lib().gp_model_forward(m, g, _ptr(logits_out)[0], _stream(stream)), "gp_model_forward")
+
+
+def gp_model_grad(m, g, labels, stream=None):
+    grad = np.zeros(MPNN_PARAMS, np.float32)
+    loss = C.c_double()
+    _check(lib().gp_model_grad(m, g, _ptr(labels)[0], grad.ctypes.data, C.byref(loss), _stream(stream)),
+           "gp_model_grad")
+    return float(loss.value), grad
+
+
+def gp_model_train_step(m, g, labels, lr, stream=None):
+    loss = C.c_double()
+    _check(lib().gp_model_train_step(m, g, _ptr(labels)[0], float(lr), C.byref(loss), _stream(stream)),
+           "gp_model_train_step")
+    return float(loss.value)
+
+
+def gp_partition_learned(g, model, part_out, logits=None, r_cpu=-1.0, tol=0.03, stream=None):
+    res = Result()
+    _check(lib().gp_partition_learned(g, model, _ptr(logits)[0], float(r_cpu), float(tol), _ptr(part_out)[0],
+                                      C.byref(res), _stream(stream)), "gp_partition_learned")
+    return res.as_dict()
 
 
 def gp_launch_count() -> int:

@@ -20,6 +20,8 @@
 #include "k_makespan.cuh"
 #include "k_batch.cuh"
 #include "k_umma.cuh"
+#include "k_mpnn.cuh"
+#include "k_propose.cuh"
 
 namespace gp {
 
@@ -254,6 +256,9 @@ struct gp_graph {
   int32_t* lo_w = nullptr;
   int32_t* lo_cC = nullptr;
   int32_t* lo_cG = nullptr;
+  int64_t* in_off = nullptr;  // vertex-indexed in-CSR (entries in no particular order within a row)
+  int32_t* in_src = nullptr;
+  int32_t* in_w = nullptr;
   LevelGraph L0;
   gp_trace trace;
   std::vector<void*> owned;
@@ -409,9 +414,9 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     g->SG = (int64_t)sg;
     // ---- transpose (in-CSR) and self-loop check
     int32_t* indeg = A.get<int32_t>(n);
-    int64_t* in_off = A.get<int64_t>(n + 1);
-    int32_t* in_src = A.get<int32_t>(m);
-    int32_t* in_w = A.get<int32_t>(m);
+    int64_t* in_off = g->in_off = g->own<int64_t>(n + 1, s);
+    int32_t* in_src = g->in_src = g->own<int32_t>(m, s);
+    int32_t* in_w = g->in_w = g->own<int32_t>(m, s);
     GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
     if (m) GP_LAUNCH(F_TRANSPOSE, k_indeg, grid_for(m, 256, 8), 256, 0, s, m, g->cols, indeg);
     scan_i32_to_i64(indeg, in_off, n, s);
