@@ -43,15 +43,24 @@ BATCH_WORKLOAD = ("4,096 DAGs, log-uniform 100..50,000 vertices, kinds in turn t
                   "tiled LU, layered (width ~sqrt(n), 8 edges per vertex to the next 1-4 layers); base seed 0")
 
 
+MODEL_PATH = os.path.join(ROOT, "paper_1502_07451_b300", "models", "mpnn3_h64.bin")
+HELD_OUT_SEEDS = (1, 2, 3)
+
+
 def _build_chunk(chunk):
     from paper_1502_07451_b300 import gen
     return [gen.build_from_spec(it) for it in chunk]
 
 
+def _build_layered_1m(seed):
+    from paper_1502_07451_b300 import gen
+    return gen.config_layered_1m(seed)
+
+
 class BatchGen:
     """Builds the batch's graphs in spawned worker processes (started before any CUDA call)."""
 
-    def __init__(self, count=BATCH_COUNT):
+    def __init__(self, count=BATCH_COUNT, held=True):
         import multiprocessing as mp
         from paper_1502_07451_b300 import gen
         self.count = count
@@ -60,15 +69,26 @@ class BatchGen:
         self.pool = mp.get_context("spawn").Pool(self.nproc)
         self.chunks = [self.spec[i::self.nproc] for i in range(self.nproc)]
         self.res = self.pool.map_async(_build_chunk, self.chunks)
+        self.held = self.pool.map_async(_build_layered_1m, HELD_OUT_SEEDS if held else ())
+
+    def held_out(self):
+        return self.held.get()
+
+    def wait(self):
+        """Block until every graph is built (no worker competes with the timed regions)."""
+        self.res.wait()
+        self.held.wait()
 
     def graphs(self):
         out = [None] * self.count
         for i, part in enumerate(self.res.get()):
             for j, g in enumerate(part):
                 out[i + j * self.nproc] = g
+        return out
+
+    def close(self):
         self.pool.close()
         self.pool.join()
-        return out
 
 
 def peaks():
@@ -223,6 +243,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="layered1m", choices=["layered1m", "batch"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered1m line")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned object of the layered1m line")
+    ap.add_argument("--profile-case", default=None, choices=["layered1m", "learned1m", "batch64"],
+                    help="run one small invocation for a profiler (no timing, no JSON line contract)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -230,8 +253,12 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     # the batch's graphs are built by spawned workers while the GPU part runs
-    bgen = BatchGen() if (args.workload == "batch" or (not args.no_batch and world == 1)) else None
+    want_batch = args.workload == "batch" or (not args.no_batch and world == 1)
+    bgen = BatchGen(held=not args.no_learned and args.workload != "batch") if want_batch else None
     if args.workload == "batch":
         run_batch_line(args, rank, world, local_rank, bgen)
         return
@@ -267,6 +294,8 @@ def main():
     for _ in range(W):
         res, ms = step()
     torch.cuda.synchronize()
+    if bgen is not None:
+        bgen.wait()
 
     # ---- timed device pass
     sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
@@ -360,10 +389,17 @@ def main():
                "sample": "the full workload, one partition + makespan (%.1f s)" % dt}
         bit_exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == res["cut"] and oms == ms)
 
+    learned = None
+    if not args.no_learned:
+        learned = bench_learned(g, dg, part, res, ms, K, W, stream, flush, bgen.held_out() if bgen else [])
     batch = None
     if bgen is not None:
         batch = bench_batch(bgen.graphs(), K, W, stream, flush, with_cpu=not args.no_cpu_baseline)
+        bgen.close()
 
+    if learned and "ms_per_step" in learned:
+        learned["plain_ms_per_step"] = total_ms / K
+        learned["speedup_vs_plain"] = (total_ms / K) / learned["ms_per_step"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -387,9 +423,87 @@ def main():
         line["cpu_baseline"] = cpu
     if batch:
         line["batch"] = batch
+    if learned:
+        line["learned"] = learned
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_learned(g, dg, part_plain, res_plain, ms_plain, K, W, stream, flush, held_out):
+    """The learned path (network proposal + refinement of level 0) on the same workload, with the
+    trained checkpoint; plus the cut against the plain path on held-out 1M-vertex layered DAGs."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    import oracle
+    if not os.path.exists(MODEL_PATH):
+        return {"unavailable": "no trained checkpoint at paper_1502_07451_b300/models/mpnn3_h64.bin"}
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    n, m = g["n"], g["m"]
+    model = gp.gp_model_load(MODEL_PATH)
+    part = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def step():
+        h = gp.gp_graph_create(n, m, *[dg[k] for k in keys], stream=stream)
+        r = gp.gp_partition_learned(h, model, part, stream=stream)
+        mk = gp.gp_makespan(h, part, None, stream)
+        gp.gp_graph_destroy(h)
+        return r, mk
+
+    for _ in range(W):
+        r, mk = step()
+    torch.cuda.synchronize()
+    tot = 0.0
+    launches0 = gp.gp_launch_count()
+    for _ in range(K):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r, mk = step()
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    launches = gp.gp_launch_count() - launches0
+    # phase split of one call (events around the network, the proposal, refinement + cut)
+    gp.gp_prof_reset()
+    gp.gp_prof_enable(True)
+    h = gp.gp_graph_create(n, m, *[dg[k] for k in keys], stream=stream)
+    rp = gp.gp_partition_learned(h, model, part, stream=stream)
+    logits = torch.empty(n, dtype=torch.float32, device="cuda")
+    gp.gp_model_forward(model, h, logits, stream)
+    gp.gp_graph_destroy(h)
+    torch.cuda.synchronize()
+    gp.gp_prof_enable(False)
+    fams = gp.kernel_families()
+    mp = gp.gp_prof_read(fams.index("mpnn"))
+    gp.gp_prof_reset()
+    # the integer result from these logits, recomputed by the oracle
+    opart, ores = oracle.partition_learned(g, logits.cpu().numpy())
+    exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == r["cut"])
+    held = []
+    for seed, hg in zip(HELD_OUT_SEEDS, held_out):
+        dh = {k: torch.from_numpy(hg[k]).cuda() for k in keys}
+        hh = gp.gp_graph_create(hg["n"], hg["m"], *[dh[k] for k in keys], stream=stream)
+        p2 = torch.empty(hg["n"], dtype=torch.uint8, device="cuda")
+        rl = gp.gp_partition_learned(hh, model, p2, stream=stream)
+        ml = gp.gp_makespan(hh, p2, None, stream)
+        rq = gp.gp_partition(hh, -1.0, 0.03, 0, p2, stream)
+        mq = gp.gp_makespan(hh, p2, None, stream)
+        gp.gp_graph_destroy(hh)
+        held.append({"seed": seed, "cut_learned": rl["cut"], "cut_plain": rq["cut"],
+                     "feasible_learned": rl["feasible"], "makespan_learned": ml, "makespan_plain": mq})
+    gp.gp_model_destroy(model)
+    return {
+        "workload": WORKLOAD, "checkpoint": "paper_1502_07451_b300/models/mpnn3_h64.bin",
+        "step": "gp_graph_create(device CSR) + gp_partition_learned (network, proposal, level-0 refinement) + "
+                "gp_makespan",
+        "value": K * m / (tot / 1e3), "unit": UNIT, "graphs_per_sec": K / (tot / 1e3), "ms_per_step": tot / K,
+        "plain_ms_per_step": None, "cut": r["cut"], "cut_plain": res_plain["cut"], "feasible": r["feasible"],
+        "makespan_ns": mk, "makespan_plain_ns": ms_plain, "rounds": r["rounds"],
+        "phase_ms": {"network": rp["ms"][0], "proposal": rp["ms"][1], "refine_and_cut": rp["ms"][2]},
+        "mpnn_kernels_ms": mp["total_ms"], "gpu_launches_per_step": int(launches / max(K, 1)),
+        "bit_exact_vs_oracle_given_logits": exact, "held_out": held,
+    }
 
 
 def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
@@ -515,6 +629,8 @@ def run_batch_line(args, rank, world, local_rank, bgen):
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
     graphs = bgen.graphs()
+    bgen.wait()
+    bgen.close()
     sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -538,3 +654,37 @@ def run_batch_line(args, rank, world, local_rank, bgen):
 
 if __name__ == "__main__":
     main()
+
+
+def run_profile_case(name):
+    """One invocation of the path, for a profiler: layered1m = one plain step (create, partition,
+    makespan) on the bench workload; learned1m = one learned step with the trained checkpoint;
+    batch64 = gp_batch_partition over 64 graphs of the batch recipe (sizes up to 10,000)."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    from paper_1502_07451_b300 import gen
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    if name in ("layered1m", "learned1m"):
+        g = gen.config_layered_1m(0)
+        dg = {k: torch.from_numpy(g[k]).cuda() for k in keys}
+        part = torch.empty(g["n"], dtype=torch.uint8, device="cuda")
+        h = gp.gp_graph_create(g["n"], g["m"], *[dg[k] for k in keys])
+        if name == "layered1m":
+            res = gp.gp_partition(h, -1.0, 0.03, 0, part)
+        else:
+            model = gp.gp_model_load(MODEL_PATH)
+            res = gp.gp_partition_learned(h, model, part)
+            gp.gp_model_destroy(model)
+        mk = gp.gp_makespan(h, part)
+        gp.gp_graph_destroy(h)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "cut": res["cut"], "makespan": mk}))
+    else:
+        graphs = [gen.build_from_spec(it) for it in gen.batch_spec(64, nmin=100, nmax=10000, base_seed=0)]
+        hs = [gp.gp_graph_create(gg["n"], gg["m"], *[torch.from_numpy(gg[k]).cuda() for k in keys]) for gg in graphs]
+        parts = [torch.empty(gg["n"], dtype=torch.uint8, device="cuda") for gg in graphs]
+        res, mks = gp.gp_batch_partition(hs, parts, makespans=True)
+        for h in hs:
+            gp.gp_graph_destroy(h)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res)}))

@@ -99,10 +99,20 @@ __device__ __forceinline__ void warp_row_sum(int64_t b, int64_t e, const int32_t
       my_u = idx[base + lane];
       my_w = ew[base + lane];
     }
-    for (int j = 0; j < cnt; j++) {
-      const int32_t u = __shfl_sync(0xffffffffu, my_u, j);
-      const float wgt = __shfl_sync(0xffffffffu, my_w, j);
-      float2 h = row(u, wgt);
+    int j = 0;
+    for (; j + 4 <= cnt; j += 4) {  // four independent row loads in flight
+      float2 h[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        h[q] = row(__shfl_sync(0xffffffffu, my_u, j + q), __shfl_sync(0xffffffffu, my_w, j + q));
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        a0 += fix_of(h[q].x);
+        a1 += fix_of(h[q].y);
+      }
+    }
+    for (; j < cnt; j++) {
+      const float2 h = row(__shfl_sync(0xffffffffu, my_u, j), __shfl_sync(0xffffffffu, my_w, j));
       a0 += fix_of(h.x);
       a1 += fix_of(h.y);
     }
