@@ -91,6 +91,29 @@ class BatchGen:
         self.pool.join()
 
 
+def profiled_traffic(family):
+    """DRAM bytes per launch of `family` from the committed ncu summary, if that summary covers this
+    family and the kernel's sources are unchanged since the capture (else None)."""
+    import hashlib
+    import glob
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_"):
+                    k, _, v = line.partition(":")
+                    kv[k.strip()] = v.strip()
+        if kv.get("traffic_kernel") != family or "traffic_bytes_per_launch" not in kv:
+            continue
+        h = hashlib.sha256()
+        for src in kv.get("traffic_sources", "").split():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest() == kv.get("traffic_sources_sha256"):
+            return float(kv["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -216,7 +239,8 @@ def run_reference(args, rank, world):
     if args.workload == "batch":
         run_reference_batch(args, rank, world)
         return
-    sample = gen.layered(100, 1000, 800_000, 0)
+    big = args.workload == "layered16m"
+    sample = gen.layered(20, 16000, 2_560_000, 0) if big else gen.layered(100, 1000, 800_000, 0)
     for _ in range(args.warmup):
         oracle_step(sample)
     tot = 0.0
@@ -224,11 +248,17 @@ def run_reference(args, rank, world):
         dt, _, _, _ = oracle_step(sample)
         tot += dt
     value = args.steps * sample["m"] / tot
-    desc = "first 100 layers of the workload recipe (100,000 vertices, 800,000 edges), oracle partition + makespan"
+    if big:
+        desc = ("first 20 layers of the 16M workload recipe (320,000 vertices, 2,560,000 edges), oracle partition "
+                "+ makespan")
+        wl = "layered DAG 1,000 layers x 16,000 vertices, 128,000,000 edges (int64 offsets), seed 0"
+    else:
+        desc = "first 100 layers of the workload recipe (100,000 vertices, 800,000 edges), oracle partition + makespan"
+        wl = WORKLOAD
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": desc}, "impl": "reference",
+            "config": {"workload": wl, "sample": desc}, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -241,7 +271,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="layered1m", choices=["layered1m", "batch"])
+    ap.add_argument("--workload", default="layered1m", choices=["layered1m", "layered16m", "batch"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered1m line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned object of the layered1m line")
     ap.add_argument("--profile-case", default=None, choices=["layered1m", "learned1m", "batch64"],
@@ -257,8 +287,8 @@ def main():
         run_profile_case(args.profile_case)
         return
     # the batch's graphs are built by spawned workers while the GPU part runs
-    want_batch = args.workload == "batch" or (not args.no_batch and world == 1)
-    bgen = BatchGen(held=not args.no_learned and args.workload != "batch") if want_batch else None
+    want_batch = args.workload == "batch" or (args.workload == "layered1m" and not args.no_batch and world == 1)
+    bgen = BatchGen(held=not args.no_learned and args.workload == "layered1m") if want_batch else None
     if args.workload == "batch":
         run_batch_line(args, rank, world, local_rank, bgen)
         return
@@ -275,7 +305,11 @@ def main():
     W = max(3, args.warmup)
     K = args.steps
     gp.lib()
-    g = gen.config_layered_1m(0)
+    big = args.workload == "layered16m"
+    global WORKLOAD
+    if big:
+        WORKLOAD = "layered DAG 1,000 layers x 16,000 vertices, 128,000,000 edges (int64 offsets), seed 0"
+    g = gen.config_layered_16m(0) if big else gen.config_layered_1m(0)
     n, m = g["n"], g["m"]
     keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
     dg = {k: torch.from_numpy(g[k]).cuda() for k in keys}
@@ -380,14 +414,21 @@ def main():
             dist.destroy_process_group()
         return
 
-    # ---- CPU baseline: the oracle on the same full workload, one core, once
+    # ---- CPU baseline: the oracle on the same full workload (1M) or its first 100 layers (16M), one core
     cpu = None
     bit_exact = None
     if not args.no_cpu_baseline and world == 1:
-        dt, opart, ores, oms = oracle_step(g)
-        cpu = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "the full workload, one partition + makespan (%.1f s)" % dt}
-        bit_exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == res["cut"] and oms == ms)
+        if big:
+            sample = gen.layered(100, 16000, 12_800_000, 0)
+            dt, _, _, _ = oracle_step(sample)
+            cpu = {"value": sample["m"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "first 100 layers of the recipe (1.6M vertices, 12.8M edges), one partition + "
+                             "makespan (%.1f s)" % dt}
+        else:
+            dt, opart, ores, oms = oracle_step(g)
+            cpu = {"value": m / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "the full workload, one partition + makespan (%.1f s)" % dt}
+            bit_exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == res["cut"] and oms == ms)
 
     learned = None
     if not args.no_learned:
@@ -400,6 +441,7 @@ def main():
     if learned and "ms_per_step" in learned:
         learned["plain_ms_per_step"] = total_ms / K
         learned["speedup_vs_plain"] = (total_ms / K) / learned["ms_per_step"]
+    traffic = profiled_traffic(dom) if not big else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -414,7 +456,9 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                     "traffic": traffic[0] if traffic else None,
+                     "traffic_source": traffic[1] if traffic else None,
                      "alg_bytes_per_launch": per_launch_bytes, "launch_ms": per_launch_ms,
                      "launches": dp["launches"]},
         "clocks": clocks,
@@ -652,9 +696,6 @@ def run_batch_line(args, rank, world, local_rank, bgen):
     print(json.dumps(line), flush=True)
 
 
-if __name__ == "__main__":
-    main()
-
 
 def run_profile_case(name):
     """One invocation of the path, for a profiler: layered1m = one plain step (create, partition,
@@ -688,3 +729,7 @@ def run_profile_case(name):
             gp.gp_graph_destroy(h)
         torch.cuda.synchronize()
         print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res)}))
+
+
+if __name__ == "__main__":
+    main()

@@ -46,9 +46,22 @@ struct MpGraph {
   int32_t nlev;
 };
 
-// fixed point in FP32 arithmetic only (scaling by a power of two is exact)
-__device__ __forceinline__ long long fix_of(float x) { return __float2ll_rn(x * 4294967296.0f); }
-__device__ __forceinline__ float unfix(long long a) { return __ll2float_rn(a) * (1.0f / 4294967296.0f); }
+// Fixed point (2^-32 units) by integer operations on the float's bits: 64-bit float/integer
+// conversions run on the FP64 pipe, which is narrow on this GPU.  Magnitudes are truncated
+// toward zero below 2^-32 and saturate beyond 2^31 (deterministic either way).
+__device__ __forceinline__ long long fix_of(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int s = (int)((b >> 23) & 0xFFu) - 118;  // |x| * 2^32 = significand * 2^s
+  if (s <= -24) return 0;                         // |x| < 2^-32, zero, subnormal
+  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
+  const unsigned long long v = s >= 0 ? (m << (s < 39 ? s : 39)) : (m >> (-s));
+  return (b >> 31) ? -(long long)v : (long long)v;
+}
+__device__ __forceinline__ float unfix(long long a) {  // two 32-bit conversions
+  const int hi = (int)(a >> 32);
+  const unsigned lo = (unsigned)(a & 0xFFFFFFFFll);
+  return (float)hi + (float)lo * (1.0f / 4294967296.0f);
+}
 
 // features, inverse degrees, per-entry edge features (out-CSR order and in-CSR order)
 __global__ void k_mp_prep(MpGraph G, float* __restrict__ X, float* __restrict__ inv_in, float* __restrict__ inv_out,
