@@ -274,7 +274,8 @@ def main():
     ap.add_argument("--workload", default="layered1m", choices=["layered1m", "layered16m", "batch"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered1m line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned object of the layered1m line")
-    ap.add_argument("--profile-case", default=None, choices=["layered1m", "learned1m", "batch64"],
+    ap.add_argument("--profile-case", default=None,
+                    choices=["layered1m", "learned1m", "batch64", "layered4m", "layered16m"],
                     help="run one small invocation for a profiler (no timing, no JSON line contract)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -699,18 +700,24 @@ def run_batch_line(args, rank, world, local_rank, bgen):
 
 def run_profile_case(name):
     """One invocation of the path, for a profiler: layered1m = one plain step (create, partition,
-    makespan) on the bench workload; learned1m = one learned step with the trained checkpoint;
-    batch64 = gp_batch_partition over 64 graphs of the batch recipe (sizes up to 10,000)."""
+    makespan) on the bench workload; layered4m / layered16m = the same on 4M / 16M-vertex layered DAGs
+    of width 16,000; learned1m = one learned step with the trained checkpoint; batch64 =
+    gp_batch_partition over 64 graphs of the batch recipe (sizes up to 10,000)."""
     import torch
     import paper_1502_07451_b300 as gp
     from paper_1502_07451_b300 import gen
     keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
-    if name in ("layered1m", "learned1m"):
-        g = gen.config_layered_1m(0)
+    if name in ("layered1m", "learned1m", "layered4m", "layered16m"):
+        if name == "layered16m":
+            g = gen.config_layered_16m(0)
+        elif name == "layered4m":
+            g = gen.layered(250, 16000, 32_000_000, 0)  # the 16M recipe's layer width, a quarter of its layers
+        else:
+            g = gen.config_layered_1m(0)
         dg = {k: torch.from_numpy(g[k]).cuda() for k in keys}
         part = torch.empty(g["n"], dtype=torch.uint8, device="cuda")
         h = gp.gp_graph_create(g["n"], g["m"], *[dg[k] for k in keys])
-        if name == "layered1m":
+        if name != "learned1m":
             res = gp.gp_partition(h, -1.0, 0.03, 0, part)
         else:
             model = gp.gp_model_load(MODEL_PATH)

@@ -483,6 +483,74 @@ __global__ void __launch_bounds__(WARPS * 32)
   account(fam, bytes, sacc);
 }
 
+// Block per row: one hash table over the block's dynamic shared memory (TMAX entries), rows of up to
+// TMAX / 2 raw entries, taken from `list`; output positions come from a block counter (any order).
+template <int TMAX>
+__global__ void k_merge_hash_blk(TwoSrc s, const int32_t* __restrict__ list, const unsigned* list_cnt,
+                                 const int64_t* __restrict__ out_start, int32_t* __restrict__ deg_out,
+                                 int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int fam) {
+  extern __shared__ __align__(16) unsigned char smem_b[];
+  __shared__ unsigned long long sacc[32];
+  __shared__ unsigned s_out;
+  unsigned long long* V = (unsigned long long*)smem_b;
+  int32_t* K = (int32_t*)(V + TMAX);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t total = (int64_t)*list_cnt;
+  unsigned long long bytes = 0;
+  for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
+    const int64_t r = list[it];
+    const RowView v = row_view(s, r);
+    const int64_t len = v.a_len + v.b_len;
+    int T = 64;
+    while (T < 2 * len) T <<= 1;
+    const int shift = 32 - (31 - __clz(T));
+    for (int i = threadIdx.x; i < T; i += blockDim.x) {
+      K[i] = kEmptyKey;
+      V[i] = 0ull;
+    }
+    if (threadIdx.x == 0) s_out = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+      int32_t col;
+      int64_t w;
+      row_entry(s, v, i, col, w);
+      bytes += entry_bytes(s, i < v.a_len);
+      if (s.drop_self && col == (int32_t)r) continue;
+      unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+      for (;;) {
+        const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+        if (old == kEmptyKey || old == col) {
+          atomicAdd(&V[slot], (unsigned long long)w);
+          break;
+        }
+        slot = (slot + 1) & (unsigned)(T - 1);
+      }
+    }
+    __syncthreads();
+    const int64_t ob = out_start[r];
+    for (int base = 0; base < T; base += blockDim.x) {
+      const int i = base + threadIdx.x;
+      const bool has = i < T && K[i] != kEmptyKey;
+      const unsigned m = __ballot_sync(0xffffffffu, has);
+      unsigned wpos = 0;
+      if (lane == 0 && m) wpos = atomicAdd(&s_out, (unsigned)__popc(m));
+      wpos = __shfl_sync(0xffffffffu, wpos, 0);
+      if (has) {
+        const unsigned pos = wpos + __popc(m & lt);
+        adj_out[ob + pos] = K[i];
+        W_out[ob + pos] = (int64_t)V[i];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      deg_out[r] = (int32_t)s_out;
+      bytes += 12ull * (unsigned long long)s_out + 24ull;
+    }
+  }
+  account(fam, bytes, sacc);
+}
+
 constexpr int kHashT1 = 256, kHashW1 = 8;    // rows of <= 128 raw entries
 constexpr int kHashT2 = 2048, kHashW2 = 4;   // rows of <= 1024 raw entries
 constexpr size_t kHashSmem1 = (size_t)kHashT1 * kHashW1 * 12;
@@ -523,17 +591,19 @@ void merge_rows(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* 
   dfree(cnts, s);
 }
 
-// Contraction merge: rows in no particular order (see k_merge_hash).
+// Contraction merge: rows in no particular order.  Tiers by raw length: a warp and a 256-entry table
+// (<= 128), a block of 256 threads and a 2,048-entry table (<= 1,024), a block of 1,024 threads and a
+// 16,384-entry table (<= 8,192), then the radix tier.
+constexpr int kHashTB2 = 2048, kHashTB3 = 16384;
+constexpr size_t kHashSmemB2 = (size_t)kHashTB2 * 12, kHashSmemB3 = (size_t)kHashTB3 * 12;
 void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* out_start,
                           int32_t* deg_out, int32_t* adj_out, int64_t* W_out, int family, int64_t raw_bound,
                           cudaStream_t s) {
   if (nrows <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    GP_CUDA(cudaFuncSetAttribute(k_merge_hash<kHashT2, kHashW2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kHashSmem2));
-    GP_CUDA(cudaFuncSetAttribute(k_merge_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kMergeBlockSmem));
+    GP_CUDA(cudaFuncSetAttribute(k_merge_hash_blk<kHashTB3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kHashSmemB3));
     attr_set = true;
   }
   unsigned* cnts = dnew<unsigned>(4, s);  // tier-2 list, tier-3 list, huge list, unused
@@ -547,11 +617,10 @@ void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const
   GP_LAUNCH(family, (k_merge_hash<kHashT1, kHashW1>), grid1, kHashW1 * 32, kHashSmem1, s, src, nrows,
             (const int32_t*)nullptr, (const unsigned*)nullptr, out_start, deg_out, adj_out, W_out, l2, cnts,
             (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
-  GP_LAUNCH(family, (k_merge_hash<kHashT2, kHashW2>), (unsigned)(2 * sms), kHashW2 * 32, kHashSmem2, s, src,
-            nrows, (const int32_t*)l2, (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, l2, cnts,
-            (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
-  GP_LAUNCH(family, k_merge_block, (unsigned)(2 * sms), kMergeBlockThreads, kMergeBlockSmem, s, src, l3, cnts + 1,
-            out_start, deg_out, adj_out, W_out, family);
+  GP_LAUNCH(family, k_merge_hash_blk<kHashTB2>, (unsigned)(8 * sms), 256, kHashSmemB2, s, src, (const int32_t*)l2,
+            (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, family);
+  GP_LAUNCH(family, k_merge_hash_blk<kHashTB3>, (unsigned)sms, 1024, kHashSmemB3, s, src, (const int32_t*)l3,
+            (const unsigned*)(cnts + 1), out_start, deg_out, adj_out, W_out, family);
   int nbits = 1;
   while (nbits < 31 && (int64_t(1) << nbits) < ncols) nbits++;
   int32_t* tk = dnew<int32_t>(raw_bound, s);
