@@ -620,6 +620,7 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     std::vector<LevelGraph> L;
     std::vector<int32_t*> cmaps;
     L.push_back(g->L0);
+    L[0].a = g->a0;
     T.n[0] = n;
     T.a[0] = g->a0;
     const int64_t capC = BC / kCapDiv, capG = BG / kCapDiv;
@@ -657,6 +658,7 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
       GP_CUDA(cudaMemcpyAsync(&ha, adev, sizeof(ha), cudaMemcpyDeviceToHost, s));
       GP_CUDA(cudaStreamSynchronize(s));
       cmaps.push_back(cmap);
+      c.a = (int64_t)ha;
       L.push_back(c);
       lev++;
       T.n[lev] = nc;

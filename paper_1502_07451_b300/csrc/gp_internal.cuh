@@ -229,6 +229,7 @@ cudaError_t launch_cluster(int family, void (*kern)(KArgs...), int csize, int bl
 struct LevelGraph {
   int64_t n = 0;
   int64_t cap = 0;       // capacity of adj / W
+  int64_t a = 0;         // entries held (0: not known, cap is used as the estimate)
   int64_t* start = nullptr;
   int32_t* deg = nullptr;
   int32_t* adj = nullptr;

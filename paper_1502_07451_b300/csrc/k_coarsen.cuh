@@ -115,16 +115,35 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
     const int64_t cv = g.vC[v], gv = g.vG[v];
     const bool nocap = cv + mC <= capC && gv + mG <= capG;
     LazyKey lk;
-    for (int32_t k = sub; k < d; k += G) {
-      const int32_t u = g.adj[b + k];
-      bytes += 8;
-      if (mate[u] != -1) continue;
-      if (!nocap) {
-        bytes += 16;
-        if (cv + g.vC[u] > capC || gv + g.vG[u] > capG) continue;
+    // four entries per lane in flight: ids and weights, then the neighbours' match state
+    for (int32_t k0 = sub; k0 < d; k0 += 4 * G) {
+      int32_t us[4];
+      int64_t ws[4];
+      bool ok[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int32_t k = k0 + q * G;
+        ok[q] = k < d;
+        us[q] = ok[q] ? g.adj[b + k] : 0;
+        ws[q] = ok[q] ? g.W[b + k] : 0;
       }
-      bytes += 8;
-      lk.offer(g.W[b + k], (uint32_t)u, seed, (uint32_t)v);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (!ok[q]) continue;
+        bytes += 16;
+        ok[q] = mate[us[q]] == -1;
+      }
+      if (!nocap) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (!ok[q]) continue;
+          bytes += 16;
+          ok[q] = cv + g.vC[us[q]] <= capC && gv + g.vG[us[q]] <= capG;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (ok[q]) lk.offer(ws[q], (uint32_t)us[q], seed, (uint32_t)v);
     }
     const EdgeKey best = group_best_key(lk.key(seed, (uint32_t)v), gmask, G);
     if (sub == 0) {
@@ -178,9 +197,21 @@ __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* 
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
     LazyKey lk;
-    for (int32_t k = sub; k < d; k += G) {
-      lk.offer(g.W[b + k], (uint32_t)g.adj[b + k], seed, (uint32_t)v);
-      bytes += 12;
+    for (int32_t k0 = sub; k0 < d; k0 += 4 * G) {  // four entries per lane in flight
+      int32_t us[4];
+      int64_t ws[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int32_t k = k0 + q * G;
+        us[q] = k < d ? g.adj[b + k] : -1;
+        ws[q] = k < d ? g.W[b + k] : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (us[q] >= 0) {
+          lk.offer(ws[q], (uint32_t)us[q], seed, (uint32_t)v);
+          bytes += 12;
+        }
     }
     const EdgeKey best = group_best_key(lk.key(seed, (uint32_t)v), gmask, G);
     if (sub == 0) {
@@ -558,6 +589,8 @@ static inline int group_for_avg(double avg) {
   if (avg <= 24.0) return 16;
   return 32;
 }
+// matching rounds: about two row entries per lane (more vertices in flight per warp)
+static inline int group_for_match(double avg) { return group_for_avg(avg * 0.5); }
 
 void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, int rounds, bool twohop,
                  int32_t* mate, cudaStream_t s) {
@@ -566,7 +599,7 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
   int32_t* pick = dnew<int32_t>(n, s);
   uint8_t* alive = dnew<uint8_t>(n, s);
   long long* maxw = dnew<long long>(2, s);
-  const int G = group_for_avg((double)g.cap / (double)n);
+  const int G = group_for_match((double)(g.a > 0 ? g.a : g.cap) / (double)n);
   GP_CUDA(cudaMemsetAsync(maxw, 0, 2 * sizeof(long long), s));
   GP_LAUNCH(F_MISC, k_match_init, grid_for(n, 256), 256, 0, s, n, g.vC, g.vG, capC, capG, mate, pick, alive);
   GP_LAUNCH(F_MISC, k_max_weights, grid_for(n, 256, 4), 256, 0, s, n, g.vC, g.vG, maxw);

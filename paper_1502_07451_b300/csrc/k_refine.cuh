@@ -132,9 +132,18 @@ __device__ void gain_all(const LevelGraph& g, const uint8_t* __restrict__ part, 
       const uint8_t p = part[v];
       const int64_t b = g.start[v];
       const int32_t d = g.deg[v];
-      for (int32_t k = sub; k < d; k += G) {
-        const long long w = g.W[b + k];
-        acc += (part[g.adj[b + k]] == p) ? -w : w;
+      for (int32_t k0 = sub; k0 < d; k0 += 4 * G) {  // four entries per lane in flight
+        int32_t us[4];
+        long long ws[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          const int32_t k = k0 + q * G;
+          us[q] = k < d ? g.adj[b + k] : -1;
+          ws[q] = k < d ? g.W[b + k] : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+          if (us[q] >= 0) acc += (part[us[q]] == p) ? -ws[q] : ws[q];
       }
       if (sub == 0) bytes += 21ull + 13ull * (unsigned long long)d;
     }
