@@ -401,6 +401,7 @@ def main():
     prof = {f: gp.gp_prof_read(i) for i, f in enumerate(fams)}
     gp.gp_prof_reset()
     hbm_peak, peak_kind = peaks()
+    hbm_peak0 = hbm_peak
     mem_fams = [f for f in fams if prof[f]["alg_bytes"] > 0]
     dom = max(mem_fams, key=lambda f: prof[f]["total_ms"])
     dp = prof[dom]
@@ -409,6 +410,11 @@ def main():
     achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
     share = {f: round(prof[f]["total_ms"] / max(sum(p["total_ms"] for p in prof.values()), 1e-9), 4)
              for f in fams if prof[f]["launches"]}
+    # every family's achieved bandwidth (algorithmic bytes / event time), as a fraction of the peak
+    by_family = {f: {"ms_per_step": round(prof[f]["total_ms"] / K, 4),
+                     "achieved_gbs": round(prof[f]["alg_bytes"] / (prof[f]["total_ms"] * 1e-3) / 1e9, 1),
+                     "frac": round(prof[f]["alg_bytes"] / (prof[f]["total_ms"] * 1e-3) / 1e9 / hbm_peak0, 4)}
+                 for f in mem_fams}
 
     if rank != 0:
         if world > 1:
@@ -452,8 +458,8 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single", "cut": res["cut"],
                    "feasible": res["feasible"], "levels": res["levels"], "makespan_ns": ms,
                    "bit_exact_vs_oracle": bit_exact, "e2e_matches_device": e2e_ok,
-                   "kernel_time_share": share, "roofline_pass": "second pass of the same K steps, "
-                   "CUDA events around every launch"},
+                   "kernel_time_share": share, "roofline_by_family": by_family,
+                   "roofline_pass": "second pass of the same K steps, CUDA events around every launch"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -84,10 +84,14 @@ __global__ void __launch_bounds__(1024)
     k_levels(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
              const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int64_t* lev_ptr,
              int32_t* level, unsigned long long* cnt, int32_t* nlev_out) {
+  __shared__ unsigned long long sacc[32];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = (int)(tid % G);
+  // algorithmic bytes: per vertex its in-range (16), counter init (4), frontier slot (4), row range
+  // (16), level-order slot and level (8); per out-entry the id (4) and the counter decrement (8)
+  unsigned long long bytes = 0;
   prefetch_l2(off, sizeof(int64_t) * (size_t)(n + 1));  // the level loop chases these: keep them in L2
   prefetch_l2(cols, sizeof(int32_t) * (size_t)off[n]);
   for (int64_t v = tid; v < n; v += stride) {
@@ -111,6 +115,7 @@ __global__ void __launch_bounds__(1024)
     for (int64_t i = beg + group; i < end; i += ngroups) {
       const int32_t v = __ldcg(lev_vtx + i);  // written by other CTAs: bypass L1
       const int64_t eb = off[v], ee = off[v + 1];
+      if (sub == 0) bytes += 48ull + 12ull * (unsigned long long)(ee - eb);
       // two out-entries per lane at a time: both decrements are in flight together
       for (int64_t e = eb + sub; e < ee; e += 2 * G) {
         const bool two = e + G < ee;
@@ -146,6 +151,7 @@ __global__ void __launch_bounds__(1024)
     *nlev_out = lev;
     cnt[3] = (unsigned long long)beg;
   }
+  account(F_LEVELS, bytes, sacc);
 }
 
 // position i of the level order: vertex, in-degree, costs
