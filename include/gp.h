@@ -318,6 +318,16 @@ GP_API gp_status gp_model_train_step(gp_model* m, const gp_graph* g, const uint8
 GP_API gp_status gp_partition_learned(gp_graph* g, const gp_model* m, const float* logits, double r_cpu,
                                       double tol, uint8_t* part_out, gp_result* res, void* stream);
 
+/* The learned path for `count` graphs: one network forward over the disjoint union of the graphs,
+ * then, per graph, exactly what gp_partition_learned(graphs[i], m, NULL, r_cpu[i], tol, ...) gives
+ * it (proposal from the graph's logits, refinement of level 0), run in the persistent batch
+ * kernel.  Arguments and outputs as gp_batch_partition (no seeds: the learned path draws nothing).
+ * Errors: GP_ERR_INVALID (arguments; a NaN logit; more than 2^31 - 1 entries in the union),
+ * GP_ERR_TIMEOUT, GP_ERR_OOM, GP_ERR_CUDA. */
+GP_API gp_status gp_batch_partition_learned(int32_t count, gp_graph* const* graphs, const gp_model* m,
+                                            const double* r_cpu, double tol, uint8_t* const* parts,
+                                            gp_result* res, int64_t* makespans, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation.
  * gp_launch_count: kernels launched by this library since load (all threads).

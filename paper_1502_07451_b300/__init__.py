@@ -109,6 +109,7 @@ def lib():
                 "gp_model_grad": [_P, _P, _P, _P, _P, _P],
                 "gp_model_train_step": [_P, _P, _P, C.c_float, _P, _P],
                 "gp_partition_learned": [_P, _P, _P, _D, _D, _P, _P, _P],
+                "gp_batch_partition_learned": [_I32, _P, _P, _P, _D, _P, _P, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -324,6 +325,21 @@ def gp_batch_partition(handles, parts, r_cpu=None, tol=0.03, seeds=None, makespa
     ms = (C.c_int64 * max(count, 1))() if makespans else None
     _check(lib().gp_batch_partition(count, hs, rc, float(tol), sd, pp, res, ms, _stream(stream)),
            "gp_batch_partition")
+    out = [res[i].as_dict() for i in range(count)]
+    return out, ([int(ms[i]) for i in range(count)] if makespans else None)
+
+
+def gp_batch_partition_learned(handles, model, parts, r_cpu=None, tol=0.03, makespans=False, stream=None):
+    """The learned path for many graphs: one network forward over their union, then the persistent
+    batch kernel (proposal + refinement of level 0 per graph).  Returns (results, makespans)."""
+    count, hs, rc, _ = _batch_args(handles, r_cpu, None)
+    if len(parts) != count:
+        raise ValueError("one split buffer per graph")
+    pp = (_P * max(count, 1))(*[_ptr(p)[0] for p in parts])
+    res = (Result * max(count, 1))()
+    ms = (C.c_int64 * max(count, 1))() if makespans else None
+    _check(lib().gp_batch_partition_learned(count, hs, model, rc, float(tol), pp, res, ms, _stream(stream)),
+           "gp_batch_partition_learned")
     out = [res[i].as_dict() for i in range(count)]
     return out, ([int(ms[i]) for i in range(count)] if makespans else None)
 

@@ -137,6 +137,7 @@ struct BatchJob {
   int idx;               // caller's index
   int64_t BC, BG;
   uint64_t seed;
+  const float* logits;   // learned path: the graph's logits (device), else null
   uint8_t* dst;          // caller's split buffer
   bool dst_host;
   size_t stage_off;
@@ -194,7 +195,9 @@ static float run_persistent(BatchCtx& c, int si, gp_graph* const* graphs, const 
     B.a0 = g->a0;
     B.BC = jobs[j].BC;
     B.BG = jobs[j].BG;
+    B.SC = g->SC;
     B.SG = g->SG;
+    B.logits = jobs[j].logits;
     B.seed = jobs[j].seed;
     B.off = g->off;
     B.cols = g->cols;
@@ -268,7 +271,7 @@ static float run_persistent(BatchCtx& c, int si, gp_graph* const* graphs, const 
 // Shared by gp_batch_partition and gp_batch_autotune: validate, plan, run with schedule si.
 static gp_status batch_run(int32_t count, gp_graph* const* graphs, const double* r_cpu, double tol,
                            const uint64_t* seeds, uint8_t* const* parts, gp_result* res, int64_t* makespans,
-                           cudaStream_t s, int si, float* kernel_ms) {
+                           cudaStream_t s, int si, float* kernel_ms, const float* const* logits_of = nullptr) {
   if (count < 0 || (count > 0 && !graphs)) return GP_ERR_INVALID;
   if (kernel_ms) *kernel_ms = 0.f;
   if (count == 0) return GP_OK;
@@ -296,6 +299,7 @@ static gp_status batch_run(int32_t count, gp_graph* const* graphs, const double*
       j.BC = BCs[i];
       j.BG = BGs[i];
       j.seed = seeds ? seeds[i] : 0ull;
+      j.logits = logits_of ? logits_of[i] : nullptr;
       j.dst = g->n > 0 ? parts[i] : nullptr;
       j.dst_host = g->n > 0 && !is_device_ptr(parts[i]);
       j.stage_off = 0;
@@ -357,7 +361,8 @@ static gp_status batch_run(int32_t count, gp_graph* const* graphs, const double*
       gp_graph* g = graphs[j.idx];
       gp_result R;
       const double r = r_cpu ? r_cpu[j.idx] : -1.0;
-      gp_status st = gp_partition(g, r, tol, j.seed, j.dst, &R, s);
+      gp_status st = j.logits ? gp_partition_learned(g, nullptr, j.logits, r, tol, j.dst, &R, s)
+                              : gp_partition(g, r, tol, j.seed, j.dst, &R, s);
       if (st != GP_OK) return st;
       if (res) res[j.idx] = R;
       if (makespans) {

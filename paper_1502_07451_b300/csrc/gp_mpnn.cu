@@ -151,6 +151,7 @@ static MpGraph mp_graph(const gp_graph* g) {
   G.cG = g->cG;
   G.level = g->level;
   G.nlev = g->nlev;
+  G.levf = nullptr;
   return G;
 }
 
@@ -590,3 +591,116 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// The learned path for many graphs: one network forward over their disjoint union, then the
+// persistent batch kernel in learned mode (proposal + refinement of level 0 per graph).
+// ------------------------------------------------------------------------------------------------
+namespace gp {
+
+// Logits of every vertex of the graphs `sel` (all with n > 0) into one device buffer; base[i] is
+// graph sel[i]'s first vertex.
+static float* mp_union_logits(const gp_model* M, gp_graph* const* graphs, const std::vector<int>& sel,
+                              std::vector<int64_t>& base, Arena& A, cudaStream_t s, int* err_dev) {
+  const int K = (int)sel.size();
+  std::vector<MpPiece> pieces(K);
+  int64_t N = 0, Mtot = 0;
+  base.assign(K, 0);
+  int32_t maxlev = 0;
+  for (int i = 0; i < K; i++) {
+    const gp_graph* g = graphs[sel[i]];
+    MpPiece& P = pieces[i];
+    P.n = g->n;
+    P.m = g->m;
+    P.vb = N;
+    P.eb = Mtot;
+    P.off = g->off;
+    P.cols = g->cols;
+    P.w = g->w;
+    P.in_off = g->in_off;
+    P.in_src = g->in_src;
+    P.in_w = g->in_w;
+    P.cC = g->cC;
+    P.cG = g->cG;
+    P.level = g->level;
+    P.nlev = g->nlev;
+    base[i] = N;
+    N += g->n;
+    Mtot += g->m;
+    maxlev = std::max(maxlev, g->nlev);
+  }
+  if (N > kMaxN || Mtot >= ((int64_t)1 << 31)) throw Fail{GP_ERR_INVALID};  // int32 ids in the union
+  MpPiece* dp = A.get<MpPiece>(K);
+  GP_CUDA(cudaMemcpyAsync(dp, pieces.data(), sizeof(MpPiece) * K, cudaMemcpyHostToDevice, s));
+  MpGraph G;
+  G.n = N;
+  G.m = Mtot;
+  int64_t* off = A.get<int64_t>(N + 1);
+  int32_t* cols = A.get<int32_t>(Mtot);
+  int32_t* w = A.get<int32_t>(Mtot);
+  int64_t* in_off = A.get<int64_t>(N + 1);
+  int32_t* in_src = A.get<int32_t>(Mtot);
+  int32_t* in_w = A.get<int32_t>(Mtot);
+  int32_t* cC = A.get<int32_t>(N);
+  int32_t* cG = A.get<int32_t>(N);
+  int32_t* level = A.get<int32_t>(N);
+  float* levf = A.get<float>(N);
+  GP_LAUNCH(F_MPNN, k_mp_union, (unsigned)std::min<int64_t>(K, (int64_t)num_sms() * 8), 256, 0, s,
+            (const MpPiece*)dp, K, off, cols, w, in_off, in_src, in_w, cC, cG, level, levf);
+  GP_LAUNCH(F_MPNN, k_mp_union_tail, 1, 1, 0, s, N, Mtot, off, in_off);
+  GP_CHECK_LAUNCH();
+  G.off = off;
+  G.cols = cols;
+  G.w = w;
+  G.in_off = in_off;
+  G.in_src = in_src;
+  G.in_w = in_w;
+  G.cC = cC;
+  G.cG = cG;
+  G.level = level;
+  G.nlev = maxlev;
+  G.levf = levf;
+  MpWork W;
+  mp_work(W, G, false, A, s);
+  mp_forward(M, G, W, nullptr, false, s);
+  GP_CUDA(cudaMemcpyAsync(err_dev, W.err, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  return W.logit;
+}
+
+}  // namespace gp
+
+extern "C" gp_status gp_batch_partition_learned(int32_t count, gp_graph* const* graphs, const gp_model* M,
+                                                const double* r_cpu, double tol, uint8_t* const* parts,
+                                                gp_result* res, int64_t* makespans, void* stream) {
+  if (count < 0 || (count > 0 && (!graphs || !M))) return GP_ERR_INVALID;
+  if (count == 0) return GP_OK;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || dev != M->dev) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> sel;
+  for (int i = 0; i < count; i++) {
+    if (!graphs[i] || graphs[i]->dev != dev) return GP_ERR_INVALID;
+    if (graphs[i]->n > 0) sel.push_back(i);
+  }
+  try {
+    pool_setup();
+    Arena A(s);
+    std::vector<const float*> lg((size_t)count, nullptr);
+    int* err = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    if (!sel.empty()) {
+      std::vector<int64_t> base;
+      const float* L = mp_union_logits(M, graphs, sel, base, A, s, err);
+      for (size_t k = 0; k < sel.size(); k++) lg[(size_t)sel[k]] = L + base[k];
+    }
+    int herr = 0;
+    GP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    if (herr) return GP_ERR_TIMEOUT;
+    return batch_run(count, graphs, r_cpu, tol, nullptr, parts, res, makespans, s, current_schedule(dev), nullptr,
+                     lg.data());
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}

@@ -20,6 +20,7 @@
 #include "k_coarsen.cuh"
 #include "k_initial.cuh"
 #include "k_refine.cuh"
+#include "k_propose.cuh"
 
 namespace gp {
 
@@ -33,8 +34,9 @@ struct BatchGraph {
   const int64_t* vC;
   const int64_t* vG;
   int64_t n, a0;
-  int64_t BC, BG, SG;
+  int64_t BC, BG, SC, SG;
   uint64_t seed;
+  const float* logits;  // not null: the learned path (proposal from these logits, refinement of level 0)
   // directed out-CSR (cut)
   const int64_t* off;
   const int32_t* cols;
@@ -561,6 +563,61 @@ __device__ void warp_grow(const LevelGraph& g, long long BC, long long BG, long 
 }
 
 // ------------------------------------------------------------------------------------------------
+// The learned proposal at CTA scope: vertices by (logit desc, id asc); the first
+// k = min(kC, kG) go to the CPU (kC: longest prefix within B_C; kG: shortest prefix after which the
+// GPU load is within B_G), found by the refinement's weighted radix selection over the keys
+// ((max - float_key(logit)) << idbits | id).  Returns false on a NaN logit.
+// ------------------------------------------------------------------------------------------------
+__device__ bool b_propose(const BatchGraph& B, const Cands& cand, uint8_t* part, long long* s_red,
+                          unsigned long long* s_redu) {
+  __shared__ unsigned long long hw[256], hc[256];
+  __shared__ SelOut so;
+  __shared__ int s_nan;
+  const int64_t n = B.n;
+  if (threadIdx.x == 0) s_nan = 0;
+  __syncthreads();
+  long long gmax = LLONG_MIN, gmin = LLONG_MAX;
+  for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const float z = B.logits[v];
+    if (isnan(z)) s_nan = 1;
+    const long long k = (long long)float_order_key(z);
+    cand.id[v] = (int32_t)v;
+    cand.gain[v] = k;
+    cand.cd[v] = B.vC[v];
+    cand.cs[v] = B.vG[v];
+    gmax = k > gmax ? k : gmax;
+    gmin = k < gmin ? k : gmin;
+  }
+  gmax = cta_max<long long>(gmax, s_red);
+  gmin = -cta_max<long long>(-gmin, s_red);
+  if (s_nan) return false;
+  const int idbits = bits_for(n);
+  const int keybits = bits_of((unsigned long long)(gmax - gmin)) + idbits;
+  const unsigned long long N = (unsigned long long)n;
+  int64_t kC = n, kG = 0;
+  if (B.SC > B.BC) {
+    block_select(cand, N, 0, B.BC, gmax, idbits, keybits, &so, hw, hc);
+    kC = so.found ? so.rank : n;
+  }
+  const long long D = B.SG - B.BG;
+  if (D > 0) {
+    block_select(cand, N, 1, D - 1, gmax, idbits, keybits, &so, hw, hc);
+    kG = so.found ? so.rank + 1 : n;
+  }
+  const int64_t k = kC < kG ? kC : kG;
+  if (k <= 0 || k >= n) {
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x) part[v] = k <= 0 ? 1 : 0;
+  } else {
+    block_select(cand, N, 2, k, gmax, idbits, keybits, &so, hw, hc);  // the candidate of rank k
+    const u128 thr = so.key;
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x)
+      part[v] = cand_key(gmax, cand.gain[v], (int32_t)v, idbits) < thr ? 0 : 1;
+  }
+  __syncthreads();
+  return true;
+}
+
+// ------------------------------------------------------------------------------------------------
 // One graph.
 // ------------------------------------------------------------------------------------------------
 template <int G>
@@ -639,9 +696,19 @@ __device__ void batch_graph(const BatchGraph& B, BatchOut* out, char* slot, unsi
   __syncthreads();
   const long long BC = B.BC, BG = B.BG;
   const long long capC = BC / kCapDiv, capG = BG / kCapDiv;
-  // ---- coarsening
   int L = 0;
+  if (B.logits) {
+    // ---- learned proposal at level 0 (no coarsening, no growing)
+    if (!b_propose(B, cand, B.part, s_red, s_redu)) {
+      if (threadIdx.x == 0) out->status = kBatchDeferred;  // the single-graph path reports the NaN
+      __syncthreads();
+      return;
+    }
+    if (threadIdx.x == 0) s_best = -1;
+  }
+  // ---- coarsening
   for (;;) {
+    if (B.logits) break;
     const LevRec f = s_lev[L];
     if (!(f.n > kCoarsest && L < kMaxLevels)) break;
     const LevelGraph g = lev_view(f);
@@ -686,7 +753,7 @@ __device__ void batch_graph(const BatchGraph& B, BatchOut* out, char* slot, unsi
     L++;
   }
   // ---- greedy growing on the coarsest level
-  {
+  if (!B.logits) {
     const LevRec f = s_lev[L];
     const LevelGraph g = lev_view(f);
     const int64_t n = f.n;

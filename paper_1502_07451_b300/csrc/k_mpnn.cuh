@@ -44,6 +44,7 @@ struct MpGraph {
   const int32_t* cG;
   const int32_t* level;
   int32_t nlev;
+  const float* levf;  // nullable: the level feature per vertex (a union of graphs with their own depths)
 };
 
 // Fixed point (2^-32 units) by integer operations on the float's bits: 64-bit float/integer
@@ -75,7 +76,7 @@ __global__ void k_mp_prep(MpGraph G, float* __restrict__ X, float* __restrict__ 
     x[1] = log1pf((float)G.cG[v]) * 0.0625f;
     x[2] = log1pf((float)id) * 0.25f;
     x[3] = log1pf((float)od) * 0.25f;
-    x[4] = (float)G.level[v] * lev_den;
+    x[4] = G.levf ? G.levf[v] : (float)G.level[v] * lev_den;
     inv_in[v] = 1.0f / (float)(id > 1 ? id : 1);
     inv_out[v] = 1.0f / (float)(od > 1 ? od : 1);
   }
@@ -390,6 +391,58 @@ __global__ void k_mp_tile_weights(const float* __restrict__ P, __nv_bfloat16* __
     Wf[(int64_t)l * per + umma_off(j, k, kHid) / 2] = x;
     Wb[(int64_t)l * per + umma_off(k, j, kCat) / 2] = x;
   }
+}
+
+}  // namespace gp
+
+namespace gp {
+
+// One graph's arrays inside a disjoint union: vertex base vb, entry base eb.
+struct MpPiece {
+  int64_t n, m, vb, eb;
+  const int64_t* off;
+  const int32_t* cols;
+  const int32_t* w;
+  const int64_t* in_off;
+  const int32_t* in_src;
+  const int32_t* in_w;
+  const int32_t* cC;
+  const int32_t* cG;
+  const int32_t* level;
+  int32_t nlev;
+};
+
+// Copies every piece into the union arrays, shifting vertex ids and row offsets (block per piece,
+// grid-strided over pieces).
+__global__ void k_mp_union(const MpPiece* __restrict__ P, int npieces, int64_t* __restrict__ off,
+                           int32_t* __restrict__ cols, int32_t* __restrict__ w, int64_t* __restrict__ in_off,
+                           int32_t* __restrict__ in_src, int32_t* __restrict__ in_w, int32_t* __restrict__ cC,
+                           int32_t* __restrict__ cG, int32_t* __restrict__ level, float* __restrict__ levf) {
+  for (int p = blockIdx.x; p < npieces; p += gridDim.x) {
+    const MpPiece Q = P[p];
+    const float den = 1.0f / (float)(Q.nlev > 1 ? Q.nlev - 1 : 1);
+    for (int64_t v = threadIdx.x; v < Q.n; v += blockDim.x) {
+      const int64_t o = Q.vb + v;
+      off[o] = Q.off[v] + Q.eb;
+      in_off[o] = Q.in_off[v] + Q.eb;
+      cC[o] = Q.cC[v];
+      cG[o] = Q.cG[v];
+      level[o] = Q.level[v];
+      levf[o] = (float)Q.level[v] * den;
+    }
+    for (int64_t e = threadIdx.x; e < Q.m; e += blockDim.x) {
+      const int64_t o = Q.eb + e;
+      cols[o] = Q.cols[e] + (int32_t)Q.vb;
+      w[o] = Q.w[e];
+      in_src[o] = Q.in_src[e] + (int32_t)Q.vb;
+      in_w[o] = Q.in_w[e];
+    }
+  }
+}
+
+__global__ void k_mp_union_tail(int64_t N, int64_t M, int64_t* off, int64_t* in_off) {
+  off[N] = M;
+  in_off[N] = M;
 }
 
 }  // namespace gp

@@ -185,3 +185,58 @@ def test_batch_invalid_arguments():
     assert L.gp_batch_partition(-1, None, None, 0.03, None, None, None, None, None) == gp.GP_ERR_INVALID
     assert L.gp_batch_partition(0, None, None, 0.03, None, None, None, None, None) == gp.GP_OK
     assert gp.lib().gp_batch_set_schedule(gp.gp_batch_schedule_count()) == gp.GP_ERR_INVALID
+
+
+MODEL = os.path.join(ROOT, "paper_1502_07451_b300", "models", "mpnn3_h64.bin")
+
+
+def test_batch_learned_equals_single_learned_and_oracle():
+    """One network forward over the union of the graphs, then the persistent kernel in learned mode:
+    every graph gets exactly gp_partition_learned's result, which is the oracle's given the logits."""
+    graphs = mixed(24, 8000, seed=31) + [gen.cholesky(4), gen.from_edges(1, [], [7], [3], [])]
+    r_cpu = [-1.0] * (len(graphs) - 3) + [0.2, 0.0, -1.0]
+    model = gp.gp_model_load(MODEL)
+    Gs = [gp.Graph(dgraph(g)) for g in graphs]
+    try:
+        parts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
+        res, ms = gp.gp_batch_partition_learned([G.h for G in Gs], model, parts, r_cpu=r_cpu, makespans=True)
+        for i, (g, G) in enumerate(zip(graphs, Gs)):
+            n = g["n"]
+            p1 = torch.zeros(max(n, 1), dtype=torch.uint8, device="cuda")
+            r1 = gp.gp_partition_learned(G.h, model, p1, r_cpu=r_cpu[i])
+            assert torch.equal(p1[:n], parts[i][:n]), i
+            assert all(r1[k] == res[i][k] for k in RES_KEYS), i
+            assert ms[i] == (G.makespan(p1[:n]) if n else 0)
+            lg = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+            if n:
+                gp.gp_model_forward(model, G.h, lg)
+            op, orr = oracle.partition_learned(g, lg.cpu().numpy()[:n], r_cpu=r_cpu[i])
+            assert np.array_equal(op, parts[i].cpu().numpy()[:n]), i
+            assert all(orr[k] == res[i][k] for k in RES_KEYS), i
+    finally:
+        for G in Gs:
+            G.close()
+        gp.gp_model_destroy(model)
+
+
+def test_batch_learned_host_buffers_and_schedules():
+    graphs = mixed(10, 3000, seed=41)
+    model = gp.gp_model_load(MODEL)
+    Gs = [gp.Graph(dgraph(g)) for g in graphs]
+    try:
+        hp = [np.zeros(g["n"], np.uint8) for g in graphs]
+        ref, _ = gp.gp_batch_partition_learned([G.h for G in Gs], model, hp)
+        try:
+            for si in range(gp.gp_batch_schedule_count()):
+                gp.gp_batch_set_schedule(si)
+                dp = [torch.zeros(g["n"], dtype=torch.uint8, device="cuda") for g in graphs]
+                res, _ = gp.gp_batch_partition_learned([G.h for G in Gs], model, dp)
+                for a, b in zip(hp, dp):
+                    assert np.array_equal(a, b.cpu().numpy())
+                assert [r["cut"] for r in res] == [r["cut"] for r in ref]
+        finally:
+            gp.gp_batch_set_schedule(-1)
+    finally:
+        for G in Gs:
+            G.close()
+        gp.gp_model_destroy(model)
