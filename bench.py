@@ -44,6 +44,8 @@ BATCH_WORKLOAD = ("4,096 DAGs, log-uniform 100..50,000 vertices, kinds in turn t
 
 
 MODEL_PATH = os.path.join(ROOT, "paper_1502_07451_b300", "models", "mpnn3_h64.bin")
+CHOL_WORKLOAD = ("1,024 tiled Cholesky task DAGs, T = 64 (45,760 tasks and 131,040 edges each), learned proposal + "
+                 "refinement + makespan per graph; the plain batched path uses seeds 0..1023")
 HELD_OUT_SEEDS = (1, 2, 3)
 
 
@@ -239,6 +241,26 @@ def run_reference(args, rank, world):
     if args.workload == "batch":
         run_reference_batch(args, rank, world)
         return
+    if args.workload == "cholesky64x1024":
+        g = gen.cholesky(64)
+        oracle_step(g)
+        tot = 0.0
+        for i in range(args.steps):
+            import oracle
+            t0 = time.perf_counter()
+            part, _ = oracle.partition(g, seed=i)
+            oracle.makespan(g, part)
+            tot += time.perf_counter() - t0
+        value = args.steps / tot
+        desc = "one tiled Cholesky T=64 DAG per step (seed = step), oracle partition + makespan"
+        line = {"metric": BATCH_METRIC, "value": value, "unit": BATCH_UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+                "config": {"workload": CHOL_WORKLOAD, "sample": desc}, "impl": "reference",
+                "cpu_baseline": {"value": value, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": BATCH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     big = args.workload == "layered16m"
     sample = gen.layered(20, 16000, 2_560_000, 0) if big else gen.layered(100, 1000, 800_000, 0)
     for _ in range(args.warmup):
@@ -271,7 +293,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="layered1m", choices=["layered1m", "layered16m", "batch"])
+    ap.add_argument("--workload", default="layered1m",
+                    choices=["layered1m", "layered16m", "batch", "cholesky64x1024"])
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered1m line")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned object of the layered1m line")
     ap.add_argument("--profile-case", default=None,
@@ -286,6 +309,9 @@ def main():
         return
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.workload == "cholesky64x1024":
+        run_cholesky_line(args, rank, world, local_rank)
         return
     # the batch's graphs are built by spawned workers while the GPU part runs
     want_batch = args.workload == "batch" or (args.workload == "layered1m" and not args.no_batch and world == 1)
@@ -592,6 +618,31 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
         tot_ms += a.elapsed_time(b)
         kern_ms += res[0]["ms"][0]
     launches = gp.gp_launch_count() - launches0
+    # the learned path for the whole batch (one network forward over the union, then the kernel)
+    learned = None
+    if os.path.exists(MODEL_PATH):
+        model = gp.gp_model_load(MODEL_PATH)
+        lparts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
+        for _ in range(W):
+            lres, _ = gp.gp_batch_partition_learned(hs, model, lparts, makespans=True, stream=stream)
+        torch.cuda.synchronize()
+        lt = 0.0
+        for _ in range(K):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            lres, lms = gp.gp_batch_partition_learned(hs, model, lparts, makespans=True, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            lt += a.elapsed_time(b)
+        gp.gp_model_destroy(model)
+        learned = {"value": K * count / (lt / 1e3), "unit": BATCH_UNIT, "ms_per_step": lt / K,
+                   "step": "gp_batch_partition_learned(4,096 resident handles, makespans on): one network "
+                           "forward over the union + the persistent kernel in learned mode",
+                   "cut_sum": int(sum(r["cut"] for r in lres)), "cut_sum_plain": int(sum(r["cut"] for r in res)),
+                   "feasible": int(sum(r["feasible"] for r in lres)),
+                   "makespan_sum": int(sum(lms)), "makespan_sum_plain": int(sum(mks))}
+        del lparts
     # achieved bandwidth of the persistent kernel: algorithmic bytes of its steps / its time
     gp.gp_prof_reset()
     gp.gp_prof_enable(True)
@@ -666,6 +717,9 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
     }
     if cpu:
         out["cpu_baseline"] = cpu
+    if learned:
+        learned["speedup_vs_plain_loop"] = learned["value"] / out["plain_graphs_per_sec"]
+        out["learned"] = learned
     return out
 
 
@@ -742,6 +796,130 @@ def run_profile_case(name):
             gp.gp_graph_destroy(h)
         torch.cuda.synchronize()
         print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res)}))
+
+
+def run_cholesky_line(args, rank, world, local_rank):
+    """1,024 tiled Cholesky DAGs with T = 64: the learned path batched (the line's value), against the
+    plain path batched and one graph after another."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    import oracle
+    from paper_1502_07451_b300 import gen
+    torch.cuda.set_device(local_rank)
+    gp.lib()
+    W = max(3, args.warmup)
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    g = gen.cholesky(64)
+    count = 1024
+    n, m = g["n"], g["m"]
+    dg = {k: torch.from_numpy(g[k]).cuda() for k in keys}
+    t0 = time.perf_counter()
+    hs = [gp.gp_graph_create(n, m, *[dg[k] for k in keys], stream=stream) for _ in range(count)]
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t0
+    parts = [torch.zeros(n, dtype=torch.uint8, device="cuda") for _ in range(count)]
+    seeds = list(range(count))
+    model = gp.gp_model_load(MODEL_PATH)
+
+    def timed(fn):
+        for _ in range(W):
+            r = fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(K):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r = fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / K, r
+
+    sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    launches0 = gp.gp_launch_count()
+    l_ms, (lres, lmk) = timed(lambda: gp.gp_batch_partition_learned(hs, model, parts, makespans=True, stream=stream))
+    launches = (gp.gp_launch_count() - launches0) // max(W + K, 1)
+    clocks = sampler.stop() if sampler else None
+    p_ms, (pres, pmk) = timed(lambda: gp.gp_batch_partition(hs, parts, seeds=seeds, makespans=True, stream=stream))
+    # the plain path, one graph after another
+    part1 = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loop_same = True
+    for i, h in enumerate(hs):
+        r = gp.gp_partition(h, -1.0, 0.03, seeds[i], part1, stream)
+        mk = gp.gp_makespan(h, part1, None, stream)
+        loop_same = loop_same and r["cut"] == pres[i]["cut"] and mk == pmk[i]
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    # batch kernel achieved bandwidth (learned mode)
+    gp.gp_prof_reset()
+    gp.gp_prof_enable(True)
+    gp.gp_batch_partition_learned(hs, model, parts, makespans=True, stream=stream)
+    torch.cuda.synchronize()
+    gp.gp_prof_enable(False)
+    fams = gp.kernel_families()
+    prof = {f: gp.gp_prof_read(i) for i, f in enumerate(fams)}
+    gp.gp_prof_reset()
+    hbm_peak, peak_kind = peaks()
+    alg = sum(p["alg_bytes"] for p in prof.values())
+    tot_ms = sum(p["total_ms"] for p in prof.values())
+    dom = max((f for f in fams if prof[f]["launches"]), key=lambda f: prof[f]["total_ms"])
+    # end to end: create from pinned host CSR, learned batch into pinned host buffers, destroy
+    hg = {k: torch.from_numpy(g[k]).pin_memory() for k in keys}
+    hparts = [torch.zeros(n, dtype=torch.uint8).pin_memory() for _ in range(count)]
+    h2d = count * sum(int(t.numel() * t.element_size()) for t in hg.values())
+    t0 = time.perf_counter()
+    hh = [gp.gp_graph_create(n, m, *[hg[k] for k in keys], stream=stream) for _ in range(count)]
+    gp.gp_batch_partition_learned(hh, model, hparts, makespans=True, stream=stream)
+    for h in hh:
+        gp.gp_graph_destroy(h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_ok = all(torch.equal(a.cpu(), b) for a, b in zip(parts, hparts))
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        opart, ores = oracle.partition(g, seed=0)
+        oracle.makespan(g, opart)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": BATCH_UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one Cholesky T=64 DAG, oracle partition + makespan (%.2f s)" % dt}
+    for h in hs:
+        gp.gp_graph_destroy(h)
+    gp.gp_model_destroy(model)
+    if rank != 0:
+        return
+    line = {"metric": BATCH_METRIC, "value": count / (l_ms / 1e3), "unit": BATCH_UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": l_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": CHOL_WORKLOAD, "l2": "flushed between timed steps (256 MB)",
+                       "step": "gp_batch_partition_learned over 1,024 resident handles, makespans on",
+                       "edges_per_sec": count * m / (l_ms / 1e3),
+                       "plain_batched_graphs_per_sec": count / (p_ms / 1e3),
+                       "plain_loop_graphs_per_sec": count / loop_s, "plain_loop_equals_batched": bool(loop_same),
+                       "cut_learned": int(lres[0]["cut"]), "cut_plain_seed0": int(pres[0]["cut"]),
+                       "cut_plain_mean": float(np.mean([r["cut"] for r in pres])),
+                       "makespan_learned": int(lmk[0]), "makespan_plain_mean": float(np.mean(pmk)),
+                       "feasible_learned": int(sum(r["feasible"] for r in lres)),
+                       "create_s": create_s, "kernel_time_share": {f: round(prof[f]["total_ms"] / tot_ms, 4)
+                                                                   for f in fams if prof[f]["launches"]}},
+            "e2e": {"value": count / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": count * (n + 56), "matches_device": bool(e2e_ok)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "kernel": dom + " (all steps of the learned batch)",
+                         "achieved": alg / (tot_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": alg / (tot_ms * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind, "traffic": None},
+            "clocks": clocks}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

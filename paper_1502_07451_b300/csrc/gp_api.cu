@@ -259,6 +259,7 @@ struct gp_graph {
   int64_t* in_off = nullptr;  // vertex-indexed in-CSR (entries in no particular order within a row)
   int32_t* in_src = nullptr;
   int32_t* in_w = nullptr;
+  bool in_sorted = false;     // in-rows sorted by (source, cost): set before the network first reads them
   LevelGraph L0;
   gp_trace trace;
   std::vector<void*> owned;

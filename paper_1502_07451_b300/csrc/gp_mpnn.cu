@@ -137,6 +137,28 @@ static void model_init_host(uint64_t seed, std::vector<float>& P) {
   fill(kPWo, kHid, std::sqrt(1.0 / kHid));
 }
 
+// Sorts the handle's in-rows by (source, cost) once, so that the network's FP32 neighbour sums run
+// in a fixed order (the transpose fills rows in no particular order).
+static void mp_prepare(const gp_graph* gc, cudaStream_t s) {
+  gp_graph* g = const_cast<gp_graph*>(gc);
+  if (g->in_sorted || g->n == 0 || g->m == 0) {
+    g->in_sorted = true;
+    return;
+  }
+  Arena A(s);
+  int32_t* long_rows = A.get<int32_t>(g->n);
+  unsigned* cnt = A.get<unsigned>(1);
+  unsigned long long* ta = A.get<unsigned long long>(g->m);
+  unsigned long long* tb = A.get<unsigned long long>(g->m);
+  GP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned), s));
+  GP_LAUNCH(F_MPNN, k_sort_rows_short, grid_for(g->n * 32, 256), 256, 0, s, g->n, (const int64_t*)g->in_off,
+            g->in_src, g->in_w, long_rows, cnt);
+  GP_LAUNCH(F_MPNN, k_sort_rows_long, (unsigned)num_sms(), 1024, 0, s, (const int64_t*)g->in_off, g->in_src,
+            g->in_w, (const int32_t*)long_rows, (const unsigned*)cnt, ta, tb);
+  GP_CHECK_LAUNCH();
+  g->in_sorted = true;
+}
+
 static MpGraph mp_graph(const gp_graph* g) {
   MpGraph G;
   G.n = g->n;
@@ -428,6 +450,7 @@ gp_status gp_model_forward(const gp_model* M, const gp_graph* g, float* logits_o
     pool_setup();
     Arena A(s);
     MpWork W;
+    mp_prepare(g, s);
     const MpGraph G = mp_graph(g);
     mp_work(W, G, false, A, s);
     mp_forward(M, G, W, nullptr, false, s);
@@ -452,6 +475,7 @@ static gp_status model_step(gp_model* M, const gp_graph* g, const uint8_t* label
     pool_setup();
     Arena A(s);
     MpWork W;
+    mp_prepare(g, s);
     const MpGraph G = mp_graph(g);
     mp_work(W, G, true, A, s);
     const uint8_t* lab = device_labels(labels, g->n, A, s);
@@ -529,6 +553,7 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
       GP_CUDA(cudaMemcpyAsync(lg, logits, sizeof(float) * n, cudaMemcpyDefault, s));
     } else {
       MpWork W;
+      mp_prepare(g, s);
       const MpGraph G = mp_graph(g);
       mp_work(W, G, false, A, s);
       mp_forward(M, G, W, nullptr, false, s);
@@ -607,6 +632,7 @@ static float* mp_union_logits(const gp_model* M, gp_graph* const* graphs, const 
   int64_t N = 0, Mtot = 0;
   base.assign(K, 0);
   int32_t maxlev = 0;
+  for (int i = 0; i < K; i++) mp_prepare(graphs[sel[i]], s);
   for (int i = 0; i < K; i++) {
     const gp_graph* g = graphs[sel[i]];
     MpPiece& P = pieces[i];

@@ -8,10 +8,10 @@
 //          e = log1p(transfer cost)/16 per directed entry
 //   h_l  = relu(c W_l + b_l), l = 1..3 (W_l 192 x 64, BF16 on the tensor cores, FP32 accumulate)
 //   logit = h3 . w_o + b_o;   loss = mean softplus(logit) - y logit
-// Neighbour sums are accumulated in 64-bit fixed point (2^-32 units), so their value does not
-// depend on the order of a row's entries: the network's outputs are deterministic.  The backward
-// pass works on the summed loss (per-vertex gradients of order one, which the fixed point needs)
-// and divides the parameter gradients by n at the end.
+// Neighbour sums run in FP32 in row order; the in-CSR's rows are sorted by (source, cost) before the
+// network first reads a graph (k_sort_rows_*) and the out-CSR's order is the caller's, so the
+// network's outputs are deterministic.  The backward pass works on the summed loss and divides the
+// parameter gradients by n at the end.
 #pragma once
 #include <cuda_bf16.h>
 
@@ -46,23 +46,6 @@ struct MpGraph {
   int32_t nlev;
   const float* levf;  // nullable: the level feature per vertex (a union of graphs with their own depths)
 };
-
-// Fixed point (2^-32 units) by integer operations on the float's bits: 64-bit float/integer
-// conversions run on the FP64 pipe, which is narrow on this GPU.  Magnitudes are truncated
-// toward zero below 2^-32 and saturate beyond 2^31 (deterministic either way).
-__device__ __forceinline__ long long fix_of(float x) {
-  const uint32_t b = __float_as_uint(x);
-  const int s = (int)((b >> 23) & 0xFFu) - 118;  // |x| * 2^32 = significand * 2^s
-  if (s <= -24) return 0;                         // |x| < 2^-32, zero, subnormal
-  const unsigned long long m = (unsigned long long)((b & 0x7FFFFFu) | 0x800000u);
-  const unsigned long long v = s >= 0 ? (m << (s < 39 ? s : 39)) : (m >> (-s));
-  return (b >> 31) ? -(long long)v : (long long)v;
-}
-__device__ __forceinline__ float unfix(long long a) {  // two 32-bit conversions
-  const int hi = (int)(a >> 32);
-  const unsigned lo = (unsigned)(a & 0xFFFFFFFFll);
-  return (float)hi + (float)lo * (1.0f / 4294967296.0f);
-}
 
 // features, inverse degrees, per-entry edge features (out-CSR order and in-CSR order)
 __global__ void k_mp_prep(MpGraph G, float* __restrict__ X, float* __restrict__ inv_in, float* __restrict__ inv_out,
@@ -100,10 +83,10 @@ __global__ void k_mp_input(int64_t n, const float* __restrict__ X, const float* 
 }
 
 // Sum over the entries [b, e) of a row of wt(entry) * rows[idx(entry)] (two features per lane, lane
-// owns features 2*lane, 2*lane+1 of a 64-wide row), in fixed point.
+// owns features 2*lane, 2*lane+1 of a 64-wide row), in row order.
 template <class RowF>
 __device__ __forceinline__ void warp_row_sum(int64_t b, int64_t e, const int32_t* __restrict__ idx,
-                                             const float* __restrict__ ew, RowF row, long long& a0, long long& a1) {
+                                             const float* __restrict__ ew, RowF row, float& a0, float& a1) {
   const int lane = threadIdx.x & 31;
   for (int64_t base = b; base < e; base += 32) {
     const int cnt = (int)((e - base) < 32 ? (e - base) : 32);
@@ -121,14 +104,14 @@ __device__ __forceinline__ void warp_row_sum(int64_t b, int64_t e, const int32_t
         h[q] = row(__shfl_sync(0xffffffffu, my_u, j + q), __shfl_sync(0xffffffffu, my_w, j + q));
 #pragma unroll
       for (int q = 0; q < 4; q++) {
-        a0 += fix_of(h[q].x);
-        a1 += fix_of(h[q].y);
+        a0 += h[q].x;
+        a1 += h[q].y;
       }
     }
     for (; j < cnt; j++) {
       const float2 h = row(__shfl_sync(0xffffffffu, my_u, j), __shfl_sync(0xffffffffu, my_w, j));
-      a0 += fix_of(h.x);
-      a1 += fix_of(h.y);
+      a0 += h.x;
+      a1 += h.y;
     }
   }
 }
@@ -148,29 +131,36 @@ __global__ void __launch_bounds__(256) k_mp_aggregate(MpGraph G, const float* __
                                                       const float* __restrict__ e_out, const float* __restrict__ e_in,
                                                       const __nv_bfloat16* __restrict__ H,
                                                       __nv_bfloat16* __restrict__ Ct) {
+  __shared__ unsigned long long sacc[32];
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const __nv_bfloat162* H2 = (const __nv_bfloat162*)H;
+  unsigned long long bytes = 0;
   auto row = [&](int32_t u, float wgt) {
     const float2 h = __bfloat1622float2(H2[(int64_t)u * 32 + lane]);
     return make_float2(wgt * h.x, wgt * h.y);
   };
   for (int64_t v = gw; v < G.n; v += nw) {
     const float2 self = __bfloat1622float2(H2[v * 32 + lane]);
-    long long i0 = 0, i1 = 0, o0 = 0, o1 = 0;
+    float i0 = 0.0f, i1 = 0.0f, o0 = 0.0f, o1 = 0.0f;
     warp_row_sum(G.in_off[v], G.in_off[v + 1], G.in_src, e_in, row, i0, i1);
     warp_row_sum(G.off[v], G.off[v + 1], G.cols, e_out, row, o0, o1);
     const float si = inv_in[v], so = inv_out[v];
     const int k = 2 * lane;
+    // per vertex: ranges (32), own row (128), inverse degrees (8), c (384); per entry: id, weight, row
+    if (lane == 0)
+      bytes += 552ull + 136ull * (unsigned long long)(G.in_off[v + 1] - G.in_off[v] + G.off[v + 1] - G.off[v]);
     store_tile2(Ct, v, k, 128, kCat, self.x, self.y);
-    store_tile2(Ct, v, kHid + k, 128, kCat, unfix(i0) * si, unfix(i1) * si);
-    store_tile2(Ct, v, 2 * kHid + k, 128, kCat, unfix(o0) * so, unfix(o1) * so);
+    store_tile2(Ct, v, kHid + k, 128, kCat, i0 * si, i1 * si);
+    store_tile2(Ct, v, 2 * kHid + k, 128, kCat, o0 * so, o1 * so);
   }
+  account(F_MPNN, bytes, sacc);
 }
 
 // forward epilogue: h = relu(acc + b), BF16 row-major
 struct EpiRelu {
+  static constexpr unsigned kOutBytes = 2;  // BF16 per output
   const float* bias;
   __nv_bfloat16* H;
   __device__ __forceinline__ void operator()(int64_t row, int col0, const float* v) const {
@@ -263,13 +253,13 @@ __global__ void __launch_bounds__(256) k_mp_agg_back(MpGraph G, const float* __r
     return make_float2(s * d.x, s * d.y);
   };
   for (int64_t v = gw; v < G.n; v += nw) {
-    long long a0 = 0, a1 = 0;
+    float a0 = 0.0f, a1 = 0.0f;
     warp_row_sum(G.off[v], G.off[v + 1], G.cols, e_out, row_in, a0, a1);
     warp_row_sum(G.in_off[v], G.in_off[v + 1], G.in_src, e_in, row_out, a0, a1);
     const float2 self = *(const float2*)(dC + v * kCat + k);
     const float2 h = __bfloat1622float2(((const __nv_bfloat162*)Hp)[v * 32 + lane]);
-    const float d0 = h.x > 0.0f ? self.x + unfix(a0) : 0.0f;
-    const float d1 = h.y > 0.0f ? self.y + unfix(a1) : 0.0f;
+    const float d0 = h.x > 0.0f ? self.x + a0 : 0.0f;
+    const float d1 = h.y > 0.0f ? self.y + a1 : 0.0f;
     dZ[v * kHid + k] = d0;
     dZ[v * kHid + k + 1] = d1;
     if (dZt) store_tile2(dZt, v, k, 128, kHid, d0, d1);
@@ -443,6 +433,126 @@ __global__ void k_mp_union(const MpPiece* __restrict__ P, int npieces, int64_t* 
 __global__ void k_mp_union_tail(int64_t N, int64_t M, int64_t* off, int64_t* in_off) {
   off[N] = M;
   in_off[N] = M;
+}
+
+}  // namespace gp
+
+namespace gp {
+
+// ------------------------------------------------------------------------------------------------
+// Deterministic row order for the network's neighbour sums: every row of a CSR (entries
+// (id, weight), int32 both) sorted by (id, weight).  Rows of <= 32 entries: a warp's shuffle
+// bitonic network; longer rows: a block's stable LSD radix sort (8-bit digits) through scratch.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long row_key(int32_t id, int32_t w) {
+  return ((unsigned long long)(uint32_t)id << 32) | (unsigned long long)(uint32_t)w;
+}
+
+__global__ void __launch_bounds__(256) k_sort_rows_short(int64_t n, const int64_t* __restrict__ off,
+                                                         int32_t* __restrict__ ids, int32_t* __restrict__ w,
+                                                         int32_t* __restrict__ long_rows, unsigned* long_cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = gw; r < n; r += nw) {
+    const int64_t b = off[r], len = off[r + 1] - b;
+    if (len <= 1) continue;
+    if (len > 32) {
+      if (lane == 0) long_rows[atomicAdd(long_cnt, 1u)] = (int32_t)r;
+      continue;
+    }
+    unsigned long long x = lane < len ? row_key(ids[b + lane], w[b + lane]) : ~0ull;
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, j);
+        const bool keep_min = ((lane & j) == 0) == ((lane & kk) == 0);
+        x = keep_min ? (x < y ? x : y) : (x > y ? x : y);
+      }
+    }
+    if (lane < len) {
+      ids[b + lane] = (int32_t)(x >> 32);
+      w[b + lane] = (int32_t)(uint32_t)x;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_sort_rows_long(const int64_t* __restrict__ off, int32_t* __restrict__ ids,
+                                                         int32_t* __restrict__ w, const int32_t* __restrict__ rows,
+                                                         const unsigned* cnt, unsigned long long* __restrict__ ta,
+                                                         unsigned long long* __restrict__ tb) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned binbase[256];
+  __shared__ int wcnt[32][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const unsigned lt = lanemask_lt();
+  const unsigned nrows = *cnt;
+  for (unsigned ri = blockIdx.x; ri < nrows; ri += gridDim.x) {
+    const int32_t r = rows[ri];
+    const int64_t b = off[r], N = off[r + 1] - b;
+    unsigned long long* src = ta + b;
+    unsigned long long* dst = tb + b;
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) src[i] = row_key(ids[b + i], w[b + i]);
+    __syncthreads();
+    for (int shift = 0; shift < 64; shift += 8) {
+      for (int x = threadIdx.x; x < 256; x += blockDim.x) hist[x] = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < N; i += blockDim.x) atomicAdd(&hist[(src[i] >> shift) & 255ull], 1u);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int x = 0; x < 256; x++) {
+          binbase[x] = run;
+          run += hist[x];
+        }
+      }
+      __syncthreads();
+      for (int64_t tile = 0; tile < N; tile += blockDim.x) {  // stable scatter, one tile at a time
+        const int64_t i = tile + threadIdx.x;
+        const bool valid = i < N;
+        for (int x = lane; x < 256; x += 32) wcnt[wid][x] = 0;
+        __syncwarp();
+        unsigned long long key = 0;
+        int dg = 0, rank = 0;
+        if (valid) {
+          key = src[i];
+          dg = (int)((key >> shift) & 255ull);
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+          const unsigned peers = __match_any_sync(act, dg);
+          rank = __popc(peers & lt);
+          if (rank == 0) wcnt[wid][dg] = __popc(peers);
+        }
+        __syncthreads();
+        unsigned tilecnt = 0;
+        if (threadIdx.x < 256) {
+          int run = 0;
+          for (int q = 0; q < nwarps; q++) {
+            const int c = wcnt[q][threadIdx.x];
+            wcnt[q][threadIdx.x] = run;
+            run += c;
+          }
+          tilecnt = (unsigned)run;
+        }
+        __syncthreads();
+        if (valid) dst[binbase[dg] + wcnt[wid][dg] + rank] = key;
+        __syncthreads();
+        if (threadIdx.x < 256) binbase[threadIdx.x] += tilecnt;
+        __syncthreads();
+      }
+      unsigned long long* t = src;
+      src = dst;
+      dst = t;
+    }
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {  // 8 passes: the result is back in ta
+      const unsigned long long k = src[i];
+      ids[b + i] = (int32_t)(k >> 32);
+      w[b + i] = (int32_t)(uint32_t)k;
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace gp

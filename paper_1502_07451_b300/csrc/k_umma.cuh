@@ -195,6 +195,12 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const uint8_t* __restrict__ A
       tmem_ld16(lane_addr + (uint32_t)(c * 16), v);
       if (row < M) epi(row, c * 16, v);
     }
+    if (threadIdx.x == 0) {  // algorithmic bytes: the A tile, the outputs (and B once per CTA)
+      const int64_t rows = (M - t * 128) < 128 ? (M - t * 128) : 128;
+      atomicAdd(&d_alg_bytes[F_MPNN], (unsigned long long)A_BYTES +
+                                          (unsigned long long)rows * N * Epi::kOutBytes +
+                                          (t == blockIdx.x ? (unsigned long long)B_BYTES : 0ull));
+    }
     tc_fence_before();
     __syncthreads();
   }
@@ -228,6 +234,7 @@ __global__ void k_umma_tile(const __nv_bfloat16* __restrict__ src, int64_t R, in
 }
 
 struct EpiStoreF32 {
+  static constexpr unsigned kOutBytes = 4;  // FP32 per output
   float* C;
   int ldc;
   __device__ __forceinline__ void operator()(int64_t row, int col0, const float* v) const {

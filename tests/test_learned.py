@@ -237,3 +237,13 @@ def test_trained_network_gains_over_the_method_without_it():
     finally:
         for G in Gs + Hs:
             G.close()
+
+
+def test_network_is_deterministic_across_handles():
+    """Two handles of the same DAG fill their in-rows in different orders; the network sorts them
+    before its first read, so the logits agree bit for bit."""
+    g = gen.layered(60, 300, 70000, 13)
+    with gp.Graph(dgraph(g)) as G1, gp.Graph(dgraph(g)) as G2, Model(seed=4) as M:
+        a = gpu_logits(M, G1, g["n"])
+        b = gpu_logits(M, G2, g["n"])
+    assert np.array_equal(a, b)
