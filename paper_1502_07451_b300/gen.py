@@ -422,10 +422,10 @@ def nearest_T(target: int, tasks_fn, lo: int, hi: int) -> int:
     return best
 
 
-def batch_spec(count: int = 4096, nmin: int = 100, nmax: int = 50000, base_seed: int = 0):
+def batch_spec(count: int = 4096, nmin: int = 100, nmax: int = 50000, base_seed: int = 0, tmax: int = 40):
     """Recipe of the mixed batch: graph i has a log-uniform target size in
-    [nmin, nmax] and kind i mod 3 (tiled Cholesky T=4..40, tiled LU, layered of
-    width ~sqrt(n) with 8 edges per vertex)."""
+    [nmin, nmax] and kind i mod 3 (tiled Cholesky T=4..tmax, tiled LU T=2..tmax,
+    layered of width ~sqrt(n) with 8 edges per vertex)."""
     u = uniform(base_seed, 9, 0, count)
     target = np.exp(math.log(nmin) + (math.log(nmax) - math.log(nmin)) * u)
     spec = []
@@ -433,9 +433,9 @@ def batch_spec(count: int = 4096, nmin: int = 100, nmax: int = 50000, base_seed:
         t = int(round(target[i]))
         kind = i % 3
         if kind == 0:
-            spec.append(("cholesky", nearest_T(t, cholesky_tasks, 4, 40), base_seed + i))
+            spec.append(("cholesky", nearest_T(t, cholesky_tasks, 4, tmax), base_seed + i))
         elif kind == 1:
-            spec.append(("lu", nearest_T(t, lu_tasks, 2, 40), base_seed + i))
+            spec.append(("lu", nearest_T(t, lu_tasks, 2, tmax), base_seed + i))
         else:
             width = max(2, int(round(math.sqrt(t))))
             layers = max(2, int(round(t / width)))

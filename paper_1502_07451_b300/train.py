@@ -3,7 +3,8 @@
   python -m paper_1502_07451_b300.train --graphs 20000 --out paper_1502_07451_b300/models/mpnn3_h64.bin
 
 Graph i of the training set follows the batch recipe (gen.batch_spec) with base seed 10^6 and
-sizes log-uniform in [--nmin, --nmax]: tiled Cholesky, tiled LU and layered DAGs in turn.  Each
+sizes log-uniform in [--nmin, --nmax]: tiled Cholesky and tiled LU (tile counts up to --tmax) and
+layered DAGs in turn.  Each
 graph is built on the host (spawned worker processes), copied to the GPU, partitioned by the plain
 multilevel path (gp_partition), and used for one Adam step of the network (gp_model_train_step),
 then released; the network is trained by the library's own forward and backward kernels.  The
@@ -33,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--seed", type=int, default=0, help="network initialisation seed")
     ap.add_argument("--base-seed", type=int, default=1_000_000)
+    ap.add_argument("--tmax", type=int, default=80, help="largest tile count of the Cholesky / LU graphs")
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None, help="write the loss curve (JSON) here")
     ap.add_argument("--workers", type=int, default=0)
@@ -43,7 +45,7 @@ def main(argv=None):
     if root not in sys.path:
         sys.path.insert(0, root)
     from paper_1502_07451_b300 import gen
-    spec = gen.batch_spec(args.graphs, nmin=args.nmin, nmax=args.nmax, base_seed=args.base_seed)
+    spec = gen.batch_spec(args.graphs, nmin=args.nmin, nmax=args.nmax, base_seed=args.base_seed, tmax=args.tmax)
     nproc = args.workers or max(1, min(32, (os.cpu_count() or 4) - 1))
     pool = mp.get_context("spawn").Pool(nproc)  # before any CUDA call
 
@@ -77,7 +79,7 @@ def main(argv=None):
         gp.gp_model_destroy(model)
         pool.close()
         pool.join()
-    summary = {"graphs": args.graphs, "epochs": args.epochs, "steps": step, "lr": args.lr,
+    summary = {"graphs": args.graphs, "epochs": args.epochs, "steps": step, "lr": args.lr, "tmax": args.tmax,
                "nmin": args.nmin, "nmax": args.nmax, "base_seed": args.base_seed, "init_seed": args.seed,
                "first_1000_loss": float(np.mean(losses[:1000])), "last_1000_loss": float(np.mean(losses[-1000:])),
                "seconds": time.time() - t0}
