@@ -194,6 +194,43 @@ struct Arena {
   }
 };
 
+// A second stream forked from `s` (it starts after everything already queued on `s`); join() makes
+// `s` wait for it, and the destructor joins too, so that frees queued on `s` afterwards (error paths
+// included) come after the side stream's work.  One side stream per device, created on first use.
+struct StreamFork {
+  cudaStream_t main, side = nullptr;
+  cudaEvent_t ev = nullptr;
+  bool joined = false;
+  explicit StreamFork(cudaStream_t s) : main(s) {
+    static std::mutex mu;
+    static cudaStream_t streams[64];
+    const int d = device_id();
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (d >= 0 && d < 64 && !streams[d]) cudaStreamCreateWithFlags(&streams[d], cudaStreamNonBlocking);
+      side = (d >= 0 && d < 64) ? streams[d] : nullptr;
+    }
+    if (!side || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      side = main;  // no second stream: run in order
+      ev = nullptr;
+      return;
+    }
+    cudaEventRecord(ev, main);
+    cudaStreamWaitEvent(side, ev, 0);
+  }
+  void join() {
+    if (joined) return;
+    joined = true;
+    if (!ev) return;
+    cudaEventRecord(ev, side);
+    cudaStreamWaitEvent(main, ev, 0);
+  }
+  ~StreamFork() {
+    join();
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+
 static bool is_device_ptr(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -425,6 +462,23 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     if (n) GP_LAUNCH(F_TRANSPOSE, k_fill_in, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off,
                      indeg, in_src, in_w, flags);
     GP_CHECK_LAUNCH();
+    // ---- symmetrisation: row v = out-row(v) + in-row(v), merged (Sec. III.B: one cost per transfer).
+    // It needs only the two CSRs, so it runs on a second stream while the level traversal (one cluster
+    // of SMs) runs on the first.
+    LevelGraph& L = g->L0;
+    L.n = n;
+    L.cap = 2 * m;
+    L.start = g->own<int64_t>(n + 1, s);
+    L.deg = g->own<int32_t>(n, s);
+    L.adj = g->own<int32_t>(2 * m, s);
+    L.W = g->own<int64_t>(2 * m, s);
+    L.vC = g->own<int64_t>(n, s);
+    L.vG = g->own<int64_t>(n, s);
+    int64_t* rawlen = A.get<int64_t>(n);
+    unsigned long long* a0 = A.get<unsigned long long>(1);
+    GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
+    StreamFork fork(s);  // the side stream starts here; its kernels are queued after the traversal
+    cudaStream_t s2 = fork.side;
     // ---- topological levels (one thread-block cluster, hardware cluster barrier per level)
     g->lev_vtx = g->own<int32_t>(n, s);
     g->lev_ptr = g->own<int64_t>(n + 2, s);
@@ -454,6 +508,25 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
       }
       if (!ok) throw Fail{GP_ERR_CUDA};
     }
+    // the symmetrisation, on the side stream, beside the traversal
+    if (n) {
+      GP_LAUNCH(F_SYM_MERGE, k_rawlen_sym, grid_for(n, 256), 256, 0, s2, n, g->off, in_off, rawlen);
+      GP_LAUNCH(F_MISC, k_widen, grid_for(n, 256), 256, 0, s2, n, g->cC, g->cG, L.vC, L.vG);
+    }
+    scan_i64(rawlen, L.start, n, s2);
+    {
+      TwoSrc src{};
+      src.a_start = g->off;
+      src.a_col = g->cols;
+      src.a_w32 = g->w;
+      src.b_start = in_off;
+      src.b_col = in_src;
+      src.b_w32 = in_w;
+      src.drop_self = 0;
+      merge_rows_unordered(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s2);
+    }
+    if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, s2, n, L.deg, a0);
+    GP_CHECK_LAUNCH();
     unsigned long long htail = 0;
     int32_t hnlev = 0;
     GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -482,35 +555,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     scan_i32_to_i64(lo_deg, g->lo_off, n, s);
     if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_fill, grid_for(n * 32, 256), 256, 0, s, n, g->lev_vtx, in_off, in_src, in_w,
                      pos_of, g->lo_off, g->lo_src, g->lo_w);
-    // ---- symmetrisation: row v = out-row(v) + in-row(v), merged (Sec. III.B: one cost per transfer)
-    LevelGraph& L = g->L0;
-    L.n = n;
-    L.cap = 2 * m;
-    L.start = g->own<int64_t>(n + 1, s);
-    L.deg = g->own<int32_t>(n, s);
-    L.adj = g->own<int32_t>(2 * m, s);
-    L.W = g->own<int64_t>(2 * m, s);
-    L.vC = g->own<int64_t>(n, s);
-    L.vG = g->own<int64_t>(n, s);
-    int64_t* rawlen = A.get<int64_t>(n);
-    if (n) {
-      GP_LAUNCH(F_SYM_MERGE, k_rawlen_sym, grid_for(n, 256), 256, 0, s, n, g->off, in_off, rawlen);
-      GP_LAUNCH(F_MISC, k_widen, grid_for(n, 256), 256, 0, s, n, g->cC, g->cG, L.vC, L.vG);
-    }
-    scan_i64(rawlen, L.start, n, s);
-    TwoSrc src{};
-    src.a_start = g->off;
-    src.a_col = g->cols;
-    src.a_w32 = g->w;
-    src.b_start = in_off;
-    src.b_col = in_src;
-    src.b_w32 = in_w;
-    src.drop_self = 0;
-    merge_rows_unordered(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s);
-    unsigned long long* a0 = A.get<unsigned long long>(1);
-    GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
-    if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, s, n, L.deg, a0);
-    GP_CHECK_LAUNCH();
+    fork.join();  // the first stream waits for the symmetrisation
     unsigned long long ha0 = 0;
     GP_CUDA(cudaMemcpyAsync(&ha0, a0, sizeof(ha0), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
