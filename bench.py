@@ -595,11 +595,21 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
     m_tot = int(sum(g["m"] for g in graphs))
     n_tot = int(sum(g["n"] for g in graphs))
     dgs = [{k: torch.from_numpy(np.ascontiguousarray(g[k])).cuda() for k in keys} for g in graphs]
+    dsrc = [dict(d, n=g["n"], m=g["m"]) for g, d in zip(graphs, dgs)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hs = [gp.gp_graph_create(g["n"], g["m"], *[d[k] for k in keys], stream=stream) for g, d in zip(graphs, dgs)]
+    hs0 = [gp.gp_graph_create(g["n"], g["m"], *[d[k] for k in keys], stream=stream) for g, d in zip(graphs, dgs)]
+    torch.cuda.synchronize()
+    create_loop_s = time.perf_counter() - t0
+    for h in hs0:
+        gp.gp_graph_destroy(h)
+    gp.gp_graph_create_batch(dsrc[:64], stream=stream)  # warm-up of the create kernel
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hs, sts = gp.gp_graph_create_batch(dsrc, stream=stream)
     torch.cuda.synchronize()
     create_s = time.perf_counter() - t0
+    assert all(st == gp.GP_OK for st in sts)
     parts = [torch.zeros(max(g["n"], 1), dtype=torch.uint8, device="cuda") for g in graphs]
     best, sched_ms = gp.gp_batch_autotune(hs, stream=stream)
     for _ in range(W):
@@ -674,8 +684,10 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
     h2d = sum(int(t.numel() * t.element_size()) for d in hgs for t in d.values())
     d2h = n_tot + count * 56  # splits + the per-graph result records
 
+    hsrc = [dict(d, n=g["n"], m=g["m"]) for g, d in zip(graphs, hgs)]
+
     def e2e_step():
-        hh = [gp.gp_graph_create(g["n"], g["m"], *[d[k] for k in keys], stream=stream) for g, d in zip(graphs, hgs)]
+        hh, _ = gp.gp_graph_create_batch(hsrc, stream=stream)
         gp.gp_batch_partition(hh, hparts, makespans=True, stream=stream)
         for h in hh:
             gp.gp_graph_destroy(h)
@@ -707,10 +719,14 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True):
         "plain_graphs_per_sec": count / plain_s, "plain_step": "gp_partition + gp_makespan per graph",
         "speedup_vs_plain": (K * count / (tot_ms / 1e3)) / (count / plain_s),
         "results_equal_plain": bool(same), "gpu_launches": int(launches),
-        "create_s": create_s,
+        "create_s": create_s, "create_step": "gp_graph_create_batch over the 4,096 device-resident CSRs "
+                                             "(one persistent launch)",
+        "create_loop_s": create_loop_s,
+        "with_create": {"graphs_per_sec": count / (create_s + tot_ms / K / 1e3),
+                        "step": "gp_graph_create_batch + gp_batch_partition"},
         "e2e": {"value": count / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "step": "gp_graph_create from pinned host CSR for every graph + gp_batch_partition into pinned "
-                        "host buffers + destroy", "matches_device": bool(e2e_ok)},
+                "step": "gp_graph_create_batch from pinned host CSRs + gp_batch_partition into pinned host "
+                        "buffers + destroy", "matches_device": bool(e2e_ok)},
         "roofline": {"bound": "hbm", "kernel": "k_batch (persistent)", "achieved": alg / (bms * 1e-3) / 1e9,
                      "peak": hbm_peak, "unit": "GB/s", "frac": alg / (bms * 1e-3) / 1e9 / hbm_peak,
                      "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg, "launch_ms": bms},

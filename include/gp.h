@@ -96,6 +96,23 @@ GP_API gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, c
 
 GP_API gp_status gp_graph_destroy(gp_graph* g);
 
+/* ---------------------------------------------------------------------------------------------
+ * gp_graph_create_batch -- gp_graph_create for `count` DAGs at once: the same checks in the same
+ * precedence, the same handle contents, one persistent kernel launch (a CTA builds one DAG at a time,
+ * largest first) instead of one call per DAG.  Arrays of `count` entries: n, m, and the five input
+ * pointers per DAG (all host memory when ptr_kind = 0, all device memory of the current device when
+ * ptr_kind = 1).  out[i] receives DAG i's handle or NULL, status[i] its own status (GP_OK,
+ * GP_ERR_INVALID, GP_ERR_OVERFLOW, GP_ERR_NOT_DAG, ...).  The handles are independent: destroy each
+ * with gp_graph_destroy (their device memory is one block, freed with the last of them).  DAGs of more
+ * than 2^20 vertices are built by gp_graph_create inside the same call.  Returns GP_OK when the call
+ * ran (check status[]), GP_ERR_INVALID for malformed arguments, GP_ERR_OOM / GP_ERR_CUDA otherwise.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_graph_create_batch(int32_t count, const int64_t* n, const int64_t* m,
+                                       const int64_t* const* offsets, const int32_t* const* cols,
+                                       const int32_t* const* edge_cost, const int32_t* const* cpu_cost,
+                                       const int32_t* const* gpu_cost, int ptr_kind, void* stream,
+                                       gp_graph** out, gp_status* status);
+
 /* Sizes of a handle: vertices, edges, undirected adjacency entries, topological levels, and the
  * summed CPU / GPU kernel times (SC, SG of Eq. (1)). Any pointer may be NULL. */
 GP_API gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* m, int64_t* a0, int32_t* nlevels,

@@ -110,6 +110,7 @@ def lib():
                 "gp_model_train_step": [_P, _P, _P, C.c_float, _P, _P],
                 "gp_partition_learned": [_P, _P, _P, _D, _D, _P, _P, _P],
                 "gp_batch_partition_learned": [_I32, _P, _P, _P, _D, _P, _P, _P, _P],
+                "gp_graph_create_batch": [_I32, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -193,6 +194,28 @@ def gp_graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, stream=N
                                C.byref(h))
     _check(st, "gp_graph_create")
     return h
+
+
+def gp_graph_create_batch(graphs, stream=None):
+    """gp_graph_create for many DAGs in one persistent launch.  graphs: dicts as for Graph (all
+    arrays on the host, or all on the device).  Returns (handles, statuses); a handle is None where
+    its status is not GP_OK."""
+    count = len(graphs)
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    ptrs = [[_ptr(g[k]) for k in keys] for g in graphs]
+    kinds = {dev for row in ptrs for (p, dev) in row if p is not None}
+    if len(kinds) > 1:
+        raise ValueError("all arrays must live on the same side (host or device)")
+    kind = 1 if kinds and kinds.pop() else 0
+    arr = lambda t, vals: (t * max(count, 1))(*vals)
+    n = arr(C.c_int64, [int(g["n"]) for g in graphs])
+    m = arr(C.c_int64, [int(g["m"]) for g in graphs])
+    cols = [arr(_P, [row[j][0] for row in ptrs]) for j in range(5)]
+    out = (_P * max(count, 1))()
+    st = (C.c_int * max(count, 1))()
+    _check(lib().gp_graph_create_batch(count, n, m, *cols, kind, _stream(stream), out, st), "gp_graph_create_batch")
+    handles = [(_P(out[i]) if st[i] == GP_OK else None) for i in range(count)]
+    return handles, [int(st[i]) for i in range(count)]
 
 
 def gp_graph_destroy(h):

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <algorithm>
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -22,6 +23,7 @@
 #include "k_umma.cuh"
 #include "k_mpnn.cuh"
 #include "k_propose.cuh"
+#include "k_create.cuh"
 
 namespace gp {
 
@@ -297,6 +299,7 @@ struct gp_graph {
   int32_t* in_src = nullptr;
   int32_t* in_w = nullptr;
   bool in_sorted = false;     // in-rows sorted by (source, cost): set before the network first reads them
+  std::shared_ptr<void> block;  // device block shared by the handles of one gp_graph_create_batch call
   LevelGraph L0;
   gp_trace trace;
   std::vector<void*> owned;
@@ -315,6 +318,7 @@ static void graph_free(gp_graph* g) {
   cudaSetDevice(g->dev);
   cudaDeviceSynchronize();
   for (void* p : g->owned) cudaFree(p);
+  g->block.reset();  // the shared block is freed with its last handle
   cudaSetDevice(cur);
   delete g;
 }

@@ -456,3 +456,235 @@ gp_status gp_batch_autotune(int32_t count, gp_graph* const* graphs, const double
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// gp_graph_create_batch: gp_graph_create for many DAGs, in one persistent launch.
+// ------------------------------------------------------------------------------------------------
+namespace gp {
+
+constexpr int64_t kCreateBatchMaxN = int64_t(1) << 20;  // larger DAGs take gp_graph_create
+constexpr int kCreateThreads = 512;
+
+struct CreateLayout {
+  size_t bytes = 0;
+  size_t add(size_t b) {
+    const size_t a = (bytes + 255) & ~(size_t)255;
+    bytes = a + (b ? b : 1);
+    return a;
+  }
+};
+
+}  // namespace gp
+
+extern "C" gp_status gp_graph_create_batch(int32_t count, const int64_t* n, const int64_t* m,
+                                           const int64_t* const* offsets, const int32_t* const* cols,
+                                           const int32_t* const* edge_cost, const int32_t* const* cpu_cost,
+                                           const int32_t* const* gpu_cost, int ptr_kind, void* stream,
+                                           gp_graph** out, gp_status* status) {
+  if (count < 0 || (count > 0 && (!n || !m || !offsets || !cols || !edge_cost || !cpu_cost || !gpu_cost || !out ||
+                                   !status)) ||
+      (ptr_kind != 0 && ptr_kind != 1))
+    return GP_ERR_INVALID;
+  for (int i = 0; i < count; i++) {
+    out[i] = nullptr;
+    status[i] = GP_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int> kern, single;
+  for (int i = 0; i < count; i++) {
+    const bool ok = n[i] >= 0 && m[i] >= 0 && n[i] <= kMaxN && offsets[i] && (m[i] == 0 || (cols[i] && edge_cost[i])) &&
+                    (n[i] == 0 || (cpu_cost[i] && gpu_cost[i]));
+    if (!ok) continue;  // status stays GP_ERR_INVALID
+    if (n[i] > kCreateBatchMaxN || m[i] >= (int64_t(1) << 31)) single.push_back(i);
+    else kern.push_back(i);
+  }
+  try {
+    pool_setup();
+    const int dev = device_id();
+    const int K = (int)kern.size();
+    if (K > 0) {
+      // one device block: every graph's inputs, then every graph's derived arrays
+      CreateLayout lay;
+      std::vector<CreateJob> jobs(K);
+      std::vector<size_t> o_in(K * 5), o_dv(K * 17);
+      for (int k = 0; k < K; k++) {
+        const int64_t nn = n[kern[k]], mm = m[kern[k]];
+        size_t* q = &o_in[k * 5];
+        q[0] = lay.add(8 * (nn + 1));
+        q[1] = lay.add(4 * mm);
+        q[2] = lay.add(4 * mm);
+        q[3] = lay.add(4 * nn);
+        q[4] = lay.add(4 * nn);
+      }
+      for (int k = 0; k < K; k++) {
+        const int64_t nn = n[kern[k]], mm = m[kern[k]];
+        size_t* q = &o_dv[k * 17];
+        const size_t sz[17] = {(size_t)(8 * (nn + 1)), (size_t)(4 * mm), (size_t)(4 * mm), (size_t)(4 * nn),
+                               (size_t)(8 * (nn + 2)), (size_t)(4 * nn), (size_t)(8 * (nn + 1)), (size_t)(4 * mm),
+                               (size_t)(4 * mm), (size_t)(4 * nn), (size_t)(4 * nn), (size_t)(8 * (nn + 1)),
+                               (size_t)(4 * nn), (size_t)(8 * mm), (size_t)(16 * mm), (size_t)(8 * nn),
+                               (size_t)(8 * nn)};
+        for (int t = 0; t < 17; t++) q[t] = lay.add(sz[t]);
+      }
+      char* base = (char*)dalloc(lay.bytes, s);
+      std::shared_ptr<void> block(base, [dev](void* p) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(dev);
+        cudaFree(p);
+        cudaSetDevice(cur);
+      });
+      int64_t nmax = 0;
+      for (int k = 0; k < K; k++) {
+        const int i = kern[k];
+        CreateJob& J = jobs[k];
+        const size_t* q = &o_in[k * 5];
+        const size_t* r = &o_dv[k * 17];
+        J.n = n[i];
+        J.m = m[i];
+        J.off = (const int64_t*)(base + q[0]);
+        J.cols = (const int32_t*)(base + q[1]);
+        J.w = (const int32_t*)(base + q[2]);
+        J.cC = (const int32_t*)(base + q[3]);
+        J.cG = (const int32_t*)(base + q[4]);
+        J.in_off = (int64_t*)(base + r[0]);
+        J.in_src = (int32_t*)(base + r[1]);
+        J.in_w = (int32_t*)(base + r[2]);
+        J.lev_vtx = (int32_t*)(base + r[3]);
+        J.lev_ptr = (int64_t*)(base + r[4]);
+        J.level = (int32_t*)(base + r[5]);
+        J.lo_off = (int64_t*)(base + r[6]);
+        J.lo_src = (int32_t*)(base + r[7]);
+        J.lo_w = (int32_t*)(base + r[8]);
+        J.lo_cC = (int32_t*)(base + r[9]);
+        J.lo_cG = (int32_t*)(base + r[10]);
+        J.start = (int64_t*)(base + r[11]);
+        J.deg = (int32_t*)(base + r[12]);
+        J.adj = (int32_t*)(base + r[13]);
+        J.W = (int64_t*)(base + r[14]);
+        J.vC = (int64_t*)(base + r[15]);
+        J.vG = (int64_t*)(base + r[16]);
+        nmax = std::max(nmax, J.n);
+      }
+      // inputs
+      if (ptr_kind == 0) {
+        for (int k = 0; k < K; k++) {
+          const int i = kern[k];
+          const CreateJob& J = jobs[k];
+          GP_CUDA(cudaMemcpyAsync((void*)J.off, offsets[i], 8 * (size_t)(J.n + 1), cudaMemcpyHostToDevice, s));
+          if (J.m) {
+            GP_CUDA(cudaMemcpyAsync((void*)J.cols, cols[i], 4 * (size_t)J.m, cudaMemcpyHostToDevice, s));
+            GP_CUDA(cudaMemcpyAsync((void*)J.w, edge_cost[i], 4 * (size_t)J.m, cudaMemcpyHostToDevice, s));
+          }
+          if (J.n) {
+            GP_CUDA(cudaMemcpyAsync((void*)J.cC, cpu_cost[i], 4 * (size_t)J.n, cudaMemcpyHostToDevice, s));
+            GP_CUDA(cudaMemcpyAsync((void*)J.cG, gpu_cost[i], 4 * (size_t)J.n, cudaMemcpyHostToDevice, s));
+          }
+        }
+      } else {
+        std::vector<CopyJob> cj(K);
+        for (int k = 0; k < K; k++) {
+          const int i = kern[k];
+          const CreateJob& J = jobs[k];
+          cj[k] = CopyJob{J.n, J.m, offsets[i], cols[i], edge_cost[i], cpu_cost[i], gpu_cost[i],
+                          (int64_t*)J.off, (int32_t*)J.cols, (int32_t*)J.w, (int32_t*)J.cC, (int32_t*)J.cG};
+        }
+        CopyJob* dcj = dnew<CopyJob>(K, s);
+        GP_CUDA(cudaMemcpyAsync(dcj, cj.data(), sizeof(CopyJob) * K, cudaMemcpyHostToDevice, s));
+        GP_LAUNCH(F_VALIDATE, k_copy_inputs, (unsigned)std::min<int64_t>(K, (int64_t)num_sms() * 8), 256, 0, s,
+                  (const CopyJob*)dcj, K);
+        GP_CHECK_LAUNCH();
+        dfree(dcj, s);
+      }
+      // the persistent launch
+      std::vector<int32_t> order(K);
+      for (int k = 0; k < K; k++) order[k] = k;
+      std::sort(order.begin(), order.end(), [&](int a, int b) {
+        const int64_t wa = jobs[a].n + jobs[a].m, wb = jobs[b].n + jobs[b].m;
+        return wa != wb ? wa > wb : a < b;
+      });
+      const int dsm = (kCreateThreads / 32) * kBatchWarpSmem;
+      auto kernfn = k_create_batch<kCreateThreads>;
+      GP_CUDA(cudaFuncSetAttribute((const void*)kernfn, cudaFuncAttributeMaxDynamicSharedMemorySize, dsm));
+      int per_sm = 0;
+      GP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernfn, kCreateThreads, dsm));
+      if (per_sm < 1) throw Fail{GP_ERR_CUDA};
+      const int slots = std::min(K, per_sm * num_sms());
+      const unsigned long long sb = ((unsigned long long)nmax * 48ull + (1ull << 16) + 255ull) & ~255ull;
+      char* ws = (char*)dalloc((size_t)slots * sb, s);
+      CreateJob* djobs = dnew<CreateJob>(K, s);
+      int32_t* dorder = dnew<int32_t>(K, s);
+      CreateOut* dout = dnew<CreateOut>(K, s);
+      unsigned* dq = dnew<unsigned>(1, s);
+      GP_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(CreateJob) * K, cudaMemcpyHostToDevice, s));
+      GP_CUDA(cudaMemcpyAsync(dorder, order.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s));
+      GP_CUDA(cudaMemsetAsync(dq, 0, sizeof(unsigned), s));
+      GP_LAUNCH(F_BATCH, kernfn, (unsigned)slots, kCreateThreads, dsm, s, (const CreateJob*)djobs,
+                (const int32_t*)dorder, K, dq, ws, sb, dout);
+      GP_CHECK_LAUNCH();
+      std::vector<CreateOut> hout(K);
+      GP_CUDA(cudaMemcpyAsync(hout.data(), dout, sizeof(CreateOut) * K, cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      dfree(ws, s);
+      dfree(djobs, s);
+      dfree(dorder, s);
+      dfree(dout, s);
+      dfree(dq, s);
+      for (int k = 0; k < K; k++) {
+        const int i = kern[k];
+        const CreateOut& o = hout[k];
+        status[i] = (gp_status)o.status;
+        if (o.status != GP_OK) continue;
+        const CreateJob& J = jobs[k];
+        gp_graph* g = new gp_graph();
+        g->dev = dev;
+        g->n = J.n;
+        g->m = J.m;
+        g->a0 = o.a0;
+        g->nlev = o.nlev;
+        g->SC = o.SC;
+        g->SG = o.SG;
+        g->max_width = o.max_width;
+        memset(&g->trace, 0, sizeof(g->trace));
+        g->off = (int64_t*)J.off;
+        g->cols = (int32_t*)J.cols;
+        g->w = (int32_t*)J.w;
+        g->cC = (int32_t*)J.cC;
+        g->cG = (int32_t*)J.cG;
+        g->in_off = J.in_off;
+        g->in_src = J.in_src;
+        g->in_w = J.in_w;
+        g->lev_vtx = J.lev_vtx;
+        g->lev_ptr = J.lev_ptr;
+        g->level = J.level;
+        g->lo_off = J.lo_off;
+        g->lo_src = J.lo_src;
+        g->lo_w = J.lo_w;
+        g->lo_cC = J.lo_cC;
+        g->lo_cG = J.lo_cG;
+        g->L0.n = J.n;
+        g->L0.cap = 2 * J.m;
+        g->L0.start = J.start;
+        g->L0.deg = J.deg;
+        g->L0.adj = J.adj;
+        g->L0.W = J.W;
+        g->L0.vC = J.vC;
+        g->L0.vG = J.vG;
+        g->block = block;
+        out[i] = g;
+      }
+    }
+    for (int i : single) status[i] = gp_graph_create(n[i], m[i], offsets[i], cols[i], edge_cost[i], cpu_cost[i],
+                                                      gpu_cost[i], ptr_kind, stream, &out[i]);
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    for (int i = 0; i < count; i++)
+      if (out[i]) {
+        gp_graph_destroy(out[i]);
+        out[i] = nullptr;
+        status[i] = f.st;
+      }
+    return f.st;
+  }
+}

@@ -309,6 +309,160 @@ __device__ void b_match(const LevelGraph& g, long long capC, long long capG, uin
 // ------------------------------------------------------------------------------------------------
 // Contraction of level f into c (c.n, c.start..c.part allocated; cap of c's rows = f.a).
 // ------------------------------------------------------------------------------------------------
+// Merges the rows of `src` (nrows of them; row r written at start[r], merged length to deg[r], in no
+// particular order): a per-warp shared-memory hash table (hash_cap entries), then one table over the
+// whole dynamic shared memory for longer rows, then a dense accumulator (acc = 0, mark = -1 on entry
+// and on exit, indexed by the mapped column) for the longest.
+__device__ void b_merge_rows(const TwoSrc& src, int64_t nrows, const int64_t* start, int32_t* deg, int32_t* adj,
+                             int64_t* W, int32_t* biglist, int64_t* acc, int32_t* mark, int hash_cap,
+                             unsigned char* dsm, int dsm_bytes, unsigned* s_cnt, int fam) {
+  if (threadIdx.x == 0) *s_cnt = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned lt = lanemask_lt();
+  unsigned long long bytes = 0;
+  // warp tier: a hash table of hash_cap entries per warp
+  {
+    unsigned long long* V = (unsigned long long*)(dsm + (size_t)wib * kBatchWarpSmem);
+    int32_t* K = (int32_t*)(V + hash_cap);
+    for (int64_t r = wib; r < nrows; r += nw) {
+      const RowView rv = row_view(src, r);
+      const int64_t len = rv.a_len + rv.b_len;
+      if (2 * len > hash_cap) {
+        if (lane == 0) biglist[atomicAdd(s_cnt, 1u)] = (int32_t)r;
+        continue;
+      }
+      int T = 32;
+      while (T < 2 * len) T <<= 1;
+      const int shift = 32 - (31 - __clz(T));
+      for (int i = lane; i < T; i += 32) {
+        K[i] = kEmptyKey;
+        V[i] = 0ull;
+      }
+      __syncwarp();
+      for (int64_t i = lane; i < len; i += 32) {
+        int32_t col;
+        int64_t w;
+        row_entry(src, rv, i, col, w);
+        bytes += 16;
+        if (src.drop_self && col == (int32_t)r) continue;
+        unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+        for (;;) {
+          const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+          if (old == kEmptyKey || old == col) {
+            atomicAdd(&V[slot], (unsigned long long)w);
+            break;
+          }
+          slot = (slot + 1) & (unsigned)(T - 1);
+        }
+      }
+      __syncwarp();
+      const int64_t ob = start[r];
+      int out = 0;
+      for (int base = 0; base < T; base += 32) {
+        const int32_t k = K[base + lane];
+        const bool has = k != kEmptyKey;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        if (has) {
+          const int pos = out + __popc(m & lt);
+          adj[ob + pos] = k;
+          W[ob + pos] = (int64_t)V[base + lane];
+        }
+        out += __popc(m);
+      }
+      if (lane == 0) {
+        deg[r] = out;
+        bytes += 12ull * (unsigned long long)out + 24ull;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const unsigned nbig = *s_cnt;
+  __syncthreads();
+  // block tier: one table over the whole dynamic shared memory; beyond it, a dense accumulator
+  // indexed by coarse id (acc = 0 and mark = -1 between rows)
+  int TB = 32;
+  while ((TB << 1) * 12 <= dsm_bytes) TB <<= 1;
+  unsigned long long* V = (unsigned long long*)dsm;
+  int32_t* K = (int32_t*)(V + TB);
+  for (unsigned bi = 0; bi < nbig; bi++) {
+    const int32_t r = biglist[bi];
+    const RowView rv = row_view(src, r);
+    const int64_t len = rv.a_len + rv.b_len;
+    const int64_t ob = start[r];
+    if (threadIdx.x == 0) *s_cnt = 0;
+    if (2 * len <= TB) {
+      int T = 32;
+      while (T < 2 * len) T <<= 1;
+      const int shift = 32 - (31 - __clz(T));
+      for (int i = threadIdx.x; i < T; i += blockDim.x) {
+        K[i] = kEmptyKey;
+        V[i] = 0ull;
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        int32_t col;
+        int64_t w;
+        row_entry(src, rv, i, col, w);
+        bytes += 16;
+        if (src.drop_self && col == r) continue;
+        unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+        for (;;) {
+          const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+          if (old == kEmptyKey || old == col) {
+            atomicAdd(&V[slot], (unsigned long long)w);
+            break;
+          }
+          slot = (slot + 1) & (unsigned)(T - 1);
+        }
+      }
+      __syncthreads();
+      for (int base = 0; base < T; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const bool has = i < T && K[i] != kEmptyKey;
+        const unsigned m = __ballot_sync(0xffffffffu, has);
+        unsigned wpos = 0;
+        if (lane == 0 && m) wpos = atomicAdd(s_cnt, (unsigned)__popc(m));
+        wpos = __shfl_sync(0xffffffffu, wpos, 0);
+        if (has) {
+          const unsigned pos = wpos + __popc(m & lt);
+          adj[ob + pos] = K[i];
+          W[ob + pos] = (int64_t)V[i];
+        }
+      }
+      __syncthreads();
+    } else {
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        int32_t col;
+        int64_t w;
+        row_entry(src, rv, i, col, w);
+        bytes += 16;
+        if (src.drop_self && col == r) continue;
+        atomicAdd((unsigned long long*)&acc[col], (unsigned long long)w);
+        if (atomicExch(&mark[col], r) != r) adj[ob + atomicAdd(s_cnt, 1u)] = col;
+      }
+      __syncthreads();
+      const unsigned k = *s_cnt;
+      for (unsigned i = threadIdx.x; i < k; i += blockDim.x) {
+        const int32_t col = adj[ob + i];
+        W[ob + i] = acc[col];
+        acc[col] = 0;
+        mark[col] = -1;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      deg[r] = (int32_t)*s_cnt;
+      bytes += 12ull * (unsigned long long)*s_cnt + 24ull;
+    }
+    __syncthreads();
+  }
+  __shared__ unsigned long long sacc[32];
+  account(fam, bytes, sacc);
+}
+
 __device__ void b_contract(const LevelGraph& f, const int32_t* mate, int32_t* cmap, int32_t* rep_of,
                            int32_t* mate_of, long long* rawlen, int32_t* biglist, int64_t* acc, int32_t* mark,
                            const LevRec& c, int hash_cap, unsigned char* dsm, int dsm_bytes, unsigned* s_cnt,
@@ -359,149 +513,8 @@ __device__ void b_contract(const LevelGraph& f, const int32_t* mate, int32_t* cm
   src.row_b = mate_of;
   src.map = cmap;
   src.drop_self = 1;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const unsigned lt = lanemask_lt();
-  unsigned long long bytes = 0;
-  // warp tier: a hash table of hash_cap entries per warp
-  {
-    unsigned long long* V = (unsigned long long*)(dsm + (size_t)wib * kBatchWarpSmem);
-    int32_t* K = (int32_t*)(V + hash_cap);
-    for (int64_t r = wib; r < nc; r += nw) {
-      const RowView rv = row_view(src, r);
-      const int64_t len = rv.a_len + rv.b_len;
-      if (2 * len > hash_cap) {
-        if (lane == 0) biglist[atomicAdd(s_cnt, 1u)] = (int32_t)r;
-        continue;
-      }
-      int T = 32;
-      while (T < 2 * len) T <<= 1;
-      const int shift = 32 - (31 - __clz(T));
-      for (int i = lane; i < T; i += 32) {
-        K[i] = kEmptyKey;
-        V[i] = 0ull;
-      }
-      __syncwarp();
-      for (int64_t i = lane; i < len; i += 32) {
-        int32_t col;
-        int64_t w;
-        row_entry(src, rv, i, col, w);
-        bytes += 16;
-        if (col == (int32_t)r) continue;
-        unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
-        for (;;) {
-          const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
-          if (old == kEmptyKey || old == col) {
-            atomicAdd(&V[slot], (unsigned long long)w);
-            break;
-          }
-          slot = (slot + 1) & (unsigned)(T - 1);
-        }
-      }
-      __syncwarp();
-      const int64_t ob = c.start[r];
-      int out = 0;
-      for (int base = 0; base < T; base += 32) {
-        const int32_t k = K[base + lane];
-        const bool has = k != kEmptyKey;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        if (has) {
-          const int pos = out + __popc(m & lt);
-          c.adj[ob + pos] = k;
-          c.W[ob + pos] = (int64_t)V[base + lane];
-        }
-        out += __popc(m);
-      }
-      if (lane == 0) {
-        c.deg[r] = out;
-        bytes += 12ull * (unsigned long long)out + 24ull;
-      }
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  const unsigned nbig = *s_cnt;
-  __syncthreads();
-  // block tier: one table over the whole dynamic shared memory; beyond it, a dense accumulator
-  // indexed by coarse id (acc = 0 and mark = -1 between rows)
-  int TB = 32;
-  while ((TB << 1) * 12 <= dsm_bytes) TB <<= 1;
-  unsigned long long* V = (unsigned long long*)dsm;
-  int32_t* K = (int32_t*)(V + TB);
-  for (unsigned bi = 0; bi < nbig; bi++) {
-    const int32_t r = biglist[bi];
-    const RowView rv = row_view(src, r);
-    const int64_t len = rv.a_len + rv.b_len;
-    const int64_t ob = c.start[r];
-    if (threadIdx.x == 0) *s_cnt = 0;
-    if (2 * len <= TB) {
-      int T = 32;
-      while (T < 2 * len) T <<= 1;
-      const int shift = 32 - (31 - __clz(T));
-      for (int i = threadIdx.x; i < T; i += blockDim.x) {
-        K[i] = kEmptyKey;
-        V[i] = 0ull;
-      }
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        int32_t col;
-        int64_t w;
-        row_entry(src, rv, i, col, w);
-        bytes += 16;
-        if (col == r) continue;
-        unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
-        for (;;) {
-          const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
-          if (old == kEmptyKey || old == col) {
-            atomicAdd(&V[slot], (unsigned long long)w);
-            break;
-          }
-          slot = (slot + 1) & (unsigned)(T - 1);
-        }
-      }
-      __syncthreads();
-      for (int base = 0; base < T; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        const bool has = i < T && K[i] != kEmptyKey;
-        const unsigned m = __ballot_sync(0xffffffffu, has);
-        unsigned wpos = 0;
-        if (lane == 0 && m) wpos = atomicAdd(s_cnt, (unsigned)__popc(m));
-        wpos = __shfl_sync(0xffffffffu, wpos, 0);
-        if (has) {
-          const unsigned pos = wpos + __popc(m & lt);
-          c.adj[ob + pos] = K[i];
-          c.W[ob + pos] = (int64_t)V[i];
-        }
-      }
-      __syncthreads();
-    } else {
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
-        int32_t col;
-        int64_t w;
-        row_entry(src, rv, i, col, w);
-        bytes += 16;
-        if (col == r) continue;
-        atomicAdd((unsigned long long*)&acc[col], (unsigned long long)w);
-        if (atomicExch(&mark[col], r) != r) c.adj[ob + atomicAdd(s_cnt, 1u)] = col;
-      }
-      __syncthreads();
-      const unsigned k = *s_cnt;
-      for (unsigned i = threadIdx.x; i < k; i += blockDim.x) {
-        const int32_t col = c.adj[ob + i];
-        c.W[ob + i] = acc[col];
-        acc[col] = 0;
-        mark[col] = -1;
-      }
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-      c.deg[r] = (int32_t)*s_cnt;
-      bytes += 12ull * (unsigned long long)*s_cnt + 24ull;
-    }
-    __syncthreads();
-  }
-  __shared__ unsigned long long sacc[32];
-  account(F_CONTRACT_MERGE, bytes, sacc);
+  b_merge_rows(src, nc, c.start, c.deg, c.adj, c.W, biglist, acc, mark, hash_cap, dsm, dsm_bytes, s_cnt,
+               F_CONTRACT_MERGE);
 }
 
 // ------------------------------------------------------------------------------------------------

@@ -240,3 +240,82 @@ def test_batch_learned_host_buffers_and_schedules():
         for G in Gs:
             G.close()
         gp.gp_model_destroy(model)
+
+
+def _export(h, g):
+    n = g["n"]
+    info = gp.gp_graph_info(h)
+    o = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    a = torch.empty(max(info["a0"], 1), dtype=torch.int32, device="cuda")
+    w = torch.empty(max(info["a0"], 1), dtype=torch.int64, device="cuda")
+    lv = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    gp.gp_graph_export(h, o, a, w, lv)
+    return info, o.cpu().numpy(), a.cpu().numpy()[:info["a0"]], w.cpu().numpy()[:info["a0"]], lv.cpu().numpy()[:n]
+
+
+def _bad_graphs():
+    ok = gen.cholesky(5)
+    bad_col = dict(ok, cols=ok["cols"].copy())
+    bad_col["cols"][3] = ok["n"] + 5
+    neg_cost = dict(ok, cpu_cost=ok["cpu_cost"].copy())
+    neg_cost["cpu_cost"][2] = -1
+    cyclic = gen.from_edges(3, [(0, 1), (1, 2), (2, 0)], [1, 1, 1], [1, 1, 1], [1, 1, 1])
+    selfloop = gen.from_edges(3, [(0, 1), (1, 1)], [1, 1, 1], [1, 1, 1], [1, 1])
+    big = 2 ** 31 - 1
+    overflow = gen.from_edges(3, [(0, 1)], [big, big, big], [1, 1, 1], [1])
+    overflow2 = gen.from_edges(2 ** 9, [], [big] * (2 ** 9), [1] * (2 ** 9), [])
+    bad_off = dict(ok, offsets=ok["offsets"].copy())
+    bad_off["offsets"][4] = bad_off["offsets"][5] + 1
+    return [bad_col, neg_cost, cyclic, selfloop, overflow, overflow2, bad_off]
+
+
+@pytest.mark.parametrize("side", ["device", "host"])
+def test_create_batch_equals_single_create(side):
+    """Statuses, sums, levels, the symmetrised graph, and everything downstream (partition, makespan,
+    the learned path) agree with gp_graph_create, DAG by DAG."""
+    graphs = mixed(30, 12000, seed=51) + [gen.from_edges(0, [], [], [], []), gen.from_edges(1, [], [7], [3], []),
+                                          gen.from_edges(1001, [(0, i) for i in range(1, 1001)], [10] * 1001,
+                                                         [5] * 1001, [1] * 1000)] + _bad_graphs()
+    src = [dgraph(g) for g in graphs] if side == "device" else graphs
+    hs, sts = gp.gp_graph_create_batch(src)
+    try:
+        for i, g in enumerate(graphs):
+            try:
+                ref = gp.Graph(dgraph(g))
+            except gp.GpError as e:
+                assert sts[i] == e.status and hs[i] is None, i
+                continue
+            with ref:
+                assert sts[i] == gp.GP_OK, (i, sts[i])
+                ib, ob, ab, wb, lb = _export(hs[i], g)
+                ir, orr, ar, wr, lr = _export(ref.h, g)
+                assert ib == ir
+                assert np.array_equal(ob, orr) and np.array_equal(ab, ar) and np.array_equal(wb, wr)
+                assert np.array_equal(lb, lr)
+                if g["n"] == 0:
+                    continue
+                p1 = torch.zeros(g["n"], dtype=torch.uint8, device="cuda")
+                p2 = torch.zeros(g["n"], dtype=torch.uint8, device="cuda")
+                r1 = gp.gp_partition(hs[i], -1.0, 0.03, 0, p1)
+                r2 = ref.partition(p2)
+                assert torch.equal(p1, p2) and all(r1[k] == r2[k] for k in RES_KEYS)
+                assert gp.gp_makespan(hs[i], p1) == ref.makespan(p2)
+    finally:
+        for h in hs:
+            if h is not None:
+                gp.gp_graph_destroy(h)
+
+
+def test_create_batch_handles_outlive_each_other():
+    graphs = mixed(6, 2000, seed=61)
+    hs, sts = gp.gp_graph_create_batch([dgraph(g) for g in graphs])
+    assert all(st == gp.GP_OK for st in sts)
+    # destroy every other handle; the rest stay usable (one shared block)
+    for h in hs[::2]:
+        gp.gp_graph_destroy(h)
+    for i in range(1, len(graphs), 2):
+        p = torch.zeros(graphs[i]["n"], dtype=torch.uint8, device="cuda")
+        r = gp.gp_partition(hs[i], -1.0, 0.03, 0, p)
+        op, orr = oracle.partition(graphs[i])
+        assert np.array_equal(p.cpu().numpy(), op) and r["cut"] == orr["cut"]
+        gp.gp_graph_destroy(hs[i])
