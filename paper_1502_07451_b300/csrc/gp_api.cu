@@ -490,6 +490,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     int32_t* rem = A.get<int32_t>(n);
     unsigned long long* tail = A.get<unsigned long long>(4);  // 3 rotating level counters + total
     int32_t* nlev_dev = A.get<int32_t>(1);
+    longlong2* frec = A.get<longlong2>(n);
     GP_CUDA(cudaMemsetAsync(tail, 0, 4 * sizeof(unsigned long long), s));
     GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), s));
     if (n) {
@@ -503,7 +504,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     if (cs > 0) {                                                                                       \
       GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, s, nn, (const int64_t*)g->off,         \
                              (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->lev_ptr, \
-                             g->level, tail, nlev_dev));                                                \
+                             g->level, tail, nlev_dev, frec));                                          \
       ok = 1;                                                                                           \
     }                                                                                                   \
   } break;

@@ -83,7 +83,7 @@ template <int G>
 __global__ void __launch_bounds__(1024)
     k_levels(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
              const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int64_t* lev_ptr,
-             int32_t* level, unsigned long long* cnt, int32_t* nlev_out) {
+             int32_t* level, unsigned long long* cnt, int32_t* nlev_out, longlong2* frec) {
   __shared__ unsigned long long sacc[32];
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(1024)
       const unsigned long long pos = atomicAdd(&cnt[0], 1ull);
       lev_vtx[pos] = (int32_t)v;
       level[v] = 0;
+      // frontier record: row start, (vertex << 32 | row length)
+      frec[pos] = make_longlong2(off[v], ((long long)v << 32) | (long long)(off[v + 1] - off[v]));
     }
   }
   cluster_sync();
@@ -113,8 +115,9 @@ __global__ void __launch_bounds__(1024)
     }
     unsigned long long* app = &cnt[(lev + 1) % 3];
     for (int64_t i = beg + group; i < end; i += ngroups) {
-      const int32_t v = __ldcg(lev_vtx + i);  // written by other CTAs: bypass L1
-      const int64_t eb = off[v], ee = off[v + 1];
+      // the record its producer wrote (row range loaded there, under that level's barrier)
+      const longlong2 rec = __ldcg(frec + i);  // written by other CTAs: bypass L1
+      const int64_t eb = rec.x, ee = eb + (rec.y & 0xFFFFFFFFll);
       if (sub == 0) bytes += 48ull + 12ull * (unsigned long long)(ee - eb);
       // two out-entries per lane at a time: both decrements are in flight together
       for (int64_t e = eb + sub; e < ee; e += 2 * G) {
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(1024)
         for (int q = 0; q < 2; q++) {
           const int32_t u = q ? u2 : u1;
           if ((q ? r2 : r1) == 1) {
+            const int64_t ub = off[u], ue = off[u + 1];  // in flight with the append below
             // warp-aggregated append: one atomic per set of lanes that got here together
             const unsigned act = __activemask();
             const int lane = threadIdx.x & 31;
@@ -137,6 +141,7 @@ __global__ void __launch_bounds__(1024)
             const unsigned long long k = base + (unsigned long long)__popc(act & ((1u << lane) - 1u));
             lev_vtx[end + (int64_t)k] = u;
             level[u] = lev + 1;
+            frec[end + (int64_t)k] = make_longlong2(ub, ((long long)u << 32) | (long long)(ue - ub));
           }
         }
       }
