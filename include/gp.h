@@ -345,6 +345,13 @@ GP_API gp_status gp_batch_partition_learned(int32_t count, gp_graph* const* grap
                                             const double* r_cpu, double tol, uint8_t* const* parts,
                                             gp_result* res, int64_t* makespans, void* stream);
 
+/* Failure-path self-check of the device waits (no fault involved): one CTA allocates tensor memory
+ * as the tensor-core product does, waits on an mbarrier that nothing arrives at with the same bounded
+ * wait (limit_ms, 1..2000), gives up, releases the tensor memory and reports it.  Returns
+ * GP_ERR_TIMEOUT when the wait gave up as designed (the context stays usable), GP_ERR_INVALID for a
+ * limit outside the range. */
+GP_API gp_status gp_selftest_wait_timeout(int32_t limit_ms, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation.
  * gp_launch_count: kernels launched by this library since load (all threads).

@@ -37,6 +37,26 @@ static gp_status step_mma(int64_t M, const void* A, const void* B, float* C, cud
 
 extern "C" {
 
+gp_status gp_selftest_wait_timeout(int32_t limit_ms, void* stream) {
+  if (limit_ms < 1 || limit_ms > 2000) return GP_ERR_INVALID;
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    int* err = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    GP_LAUNCH(F_MISC, k_wait_selftest, 1, 128, 0, s, (uint64_t)limit_ms * 1000000ull, err);
+    GP_CHECK_LAUNCH();
+    int herr = 0;
+    GP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    return herr ? GP_ERR_TIMEOUT : GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
 gp_status gp_step_mma_bf16(int64_t M, int32_t N, int32_t K, const void* A, const void* B, float* C, void* stream) {
   if (M < 0 || M > kMaxN || (M > 0 && (!A || !B || !C))) return GP_ERR_INVALID;
   if (M > 0 && (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C))) return GP_ERR_INVALID;

@@ -216,6 +216,31 @@ __global__ void __launch_bounds__(128) k_umma_gemm(const uint8_t* __restrict__ A
   if (warp == 0) tmem_dealloc(taddr, NCOLS);
 }
 
+// Failure-path check of the bounded waits: allocates tensor memory as the GEMM does, waits on an
+// mbarrier that nothing arrives at (limit `limit_ns`), then releases the tensor memory and records
+// the timeout, leaving the context usable.
+__global__ void __launch_bounds__(128) k_wait_selftest(uint64_t limit_ns, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_taddr;
+  __shared__ int s_fail;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) tmem_alloc(&s_taddr, 32);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (!mbar_wait(&bar, 0, limit_ns)) s_fail = 1;  // no arrival: the wait must give up
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (threadIdx.x == 0 && s_fail) atomicOr(err, kUmmaErrTimeout);
+  if (warp == 0) tmem_dealloc(s_taddr, 32);
+}
+
 template <int N, int K>
 constexpr size_t umma_smem_bytes() {
   return 128u * K * 2u + (size_t)N * K * 2u;

@@ -36,3 +36,16 @@ def test_mma_rejects_bad_shapes():
     assert e.value.status == gp.GP_ERR_INVALID
     with pytest.raises(gp.GpError):
         gp.gp_step_mma_bf16(A.cpu(), B.cpu(), C.cpu())
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A device wait on an mbarrier that nothing arrives at gives up after its limit and reports
+    GP_ERR_TIMEOUT; tensor memory is released and the next product runs normally."""
+    L = gp.lib()
+    assert L.gp_selftest_wait_timeout(50, None) == gp.GP_ERR_TIMEOUT
+    assert L.gp_selftest_wait_timeout(0, None) == gp.GP_ERR_INVALID
+    A = torch.randn(256, 192).to(torch.bfloat16).cuda()
+    B = torch.randn(192, 64).to(torch.bfloat16).cuda()
+    C = torch.empty(256, 64, device="cuda")
+    gp.gp_step_mma_bf16(A, B, C)
+    assert torch.allclose(C.double(), A.double() @ B.double(), rtol=1e-3, atol=1e-3)
