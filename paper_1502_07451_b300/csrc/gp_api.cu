@@ -323,18 +323,35 @@ static void graph_free(gp_graph* g) {
   delete g;
 }
 
-// The makespan kernel in one cluster sized to the widest level (G lanes per vertex).
+// The makespan kernel in one cluster sized to the widest level (G lanes per vertex): the
+// distributed-shared-memory ring variant when two adjacent levels fit its ring, else (or when
+// GP_MAKESPAN_KERNEL=cluster) the variant that reads every predecessor from global memory.
 static cudaError_t launch_makespan(const gp_graph* g, const uint8_t* part, unsigned long long* fp,
                                    unsigned long long* ms, int* bad, int64_t* fin, cudaStream_t s) {
   const int G = makespan_group(g->n, g->m);
   const int32_t nlev = g->nlev;
+  const char* forced = getenv("GP_MAKESPAN_KERNEL");
+  const bool dsm = g->max_width <= kMsR && g->m < ((int64_t)1 << 31) && g->n < ((int64_t)1 << 31) &&
+                   !(forced && strcmp(forced, "cluster") == 0);
   switch (G) {
 #define GP_MS(GG)                                                                                      \
   case GG: {                                                                                           \
-    const int cmax = cluster_max((const void*)k_makespan<GG>, 1024, 0);                                \
+    if (dsm) {                                                                                         \
+      const cudaError_t e = cudaFuncSetAttribute(k_makespan_dsm<GG>,                                   \
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMsRingBytes); \
+      if (e != cudaSuccess) return e;                                                                  \
+    }                                                                                                  \
+    const int cmax = dsm ? cluster_max((const void*)k_makespan_dsm<GG>, 1024, kMsRingBytes)            \
+                         : cluster_max((const void*)k_makespan<GG>, 1024, 0);                          \
     if (cmax <= 0) return cudaErrorLaunchFailure;                                                      \
     int64_t want = (g->max_width * GG + 1023) / 1024;                                                  \
+    if (dsm && want > 8) want = 8; /* each value goes to every CTA: 8 measured fastest at 1,000-wide levels */ \
     const int cs = (int)(want < 1 ? 1 : (want < cmax ? want : cmax));                                  \
+    if (dsm)                                                                                           \
+      return launch_cluster(F_MAKESPAN, k_makespan_dsm<GG>, cs, 1024, kMsRingBytes, s, nlev,           \
+                            (const int64_t*)g->lev_ptr, (const int32_t*)g->lev_vtx, (const int64_t*)g->lo_off, \
+                            (const int32_t*)g->lo_src, (const int32_t*)g->lo_w, (const int32_t*)g->lo_cC, \
+                            (const int32_t*)g->lo_cG, part, fp, ms, bad, fin);                         \
     return launch_cluster(F_MAKESPAN, k_makespan<GG>, cs, 1024, 0, s, nlev, (const int64_t*)g->lev_ptr, \
                           (const int32_t*)g->lev_vtx, (const int64_t*)g->lo_off, (const int32_t*)g->lo_src, \
                           (const int32_t*)g->lo_w, (const int32_t*)g->lo_cC, (const int32_t*)g->lo_cG, part, \
@@ -853,6 +870,7 @@ gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan,
     GP_CUDA(cudaMemcpyAsync(&h, sm, sizeof(Small), cudaMemcpyDeviceToHost, s));
     if (fin_host) GP_CUDA(cudaMemcpyAsync(finish_out, fin, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
+    if (h.bad & 2) return GP_ERR_TIMEOUT;  // a bounded device wait gave up
     if (h.bad) return GP_ERR_INVALID;
     *makespan = (int64_t)h.ms;
     return GP_OK;

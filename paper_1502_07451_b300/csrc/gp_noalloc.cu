@@ -60,7 +60,7 @@ extern "C" gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part,
   if (st != GP_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* msp = base;                  // word 0: makespan
-  int* badp = (int*)(base + 1);                    // word 1: a part value > 1 was seen
+  int* badp = (int*)(base + 1);                    // word 1: bit 0 a part value > 1, bit 1 a wait gave up
   unsigned long long* fp = base + 8;               // finish times, written before they are read
   // the control words must start at zero; the finish area needs no clearing
   if (cudaMemsetAsync(base, 0, 8 * sizeof(unsigned long long), s) != cudaSuccess) {
@@ -77,6 +77,7 @@ extern "C" gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part,
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
+  if ((int)ctl[1] & 2) return GP_ERR_TIMEOUT;  // a bounded device wait gave up
   if ((int)ctl[1]) return GP_ERR_INVALID;
   *makespan = (int64_t)ctl[0];
   return GP_OK;

@@ -294,6 +294,47 @@ def test_makespan_random_mappings():
                 assert ms == oms and np.array_equal(host(fin), ofin)
 
 
+def _long_range_chain(n, stride, seed):
+    """A chain 0 -> 1 -> ... -> n-1 (one vertex per level) with extra edges from every stride-th
+    vertex to vertices 9,000 to 11,000 positions later: predecessors further back than any ring."""
+    rng = np.random.default_rng(seed)
+    edges = [(i, i + 1) for i in range(n - 1)]
+    for u in range(0, n - 11000, stride):
+        edges.append((u, u + int(rng.integers(9000, 11000))))
+    ne = len(edges)
+    return gen.from_edges(n, edges, rng.integers(1, 1000, n).tolist(), rng.integers(1, 1000, n).tolist(),
+                          rng.integers(1, 5000, ne).tolist())
+
+
+def test_makespan_kernels_agree_with_oracle():
+    """Both makespan kernels (by default the cluster kernel with a distributed-shared-memory ring of
+    recent finish times, exchanged by st.async, where every level fits it; GP_MAKESPAN_KERNEL=cluster: every
+    predecessor from global memory) on graphs that reach each branch: levels narrow enough for the
+    ring, levels too wide for it, predecessors beyond the ring, one-vertex levels, several lanes per
+    vertex, levels wider than the cluster's groups."""
+    graphs = [gen.layered(30, 1000, 240000, 1), gen.layered(12, 3000, 300000, 2), gen.layered(6, 5000, 200000, 9),
+              gen.layered(4, 1500, 60000, 3), gen.random_dag(3000, 12000, 4), gen.random_dag(300, 12000, 6),
+              _long_range_chain(30000, 97, 5), FIXTURES["hub1000"](), gen.cholesky(16)]
+    old = os.environ.get("GP_MAKESPAN_KERNEL")
+    try:
+        for i, g in enumerate(graphs):
+            rng = np.random.default_rng(100 + i)
+            p = rng.integers(0, 2, g["n"]).astype(np.uint8)
+            oms, ofin = oracle.makespan(g, p, with_finish=True)
+            with gp.Graph(dgraph(g)) as G:
+                for kern in ("default", "cluster"):
+                    os.environ["GP_MAKESPAN_KERNEL"] = kern
+                    fin = torch.empty(g["n"], dtype=torch.int64, device="cuda")
+                    assert G.makespan(dev(p), fin) == oms, (i, kern)
+                    assert np.array_equal(host(fin), ofin), (i, kern)
+                    assert G.makespan(dev(p)) == oms, (i, kern)
+    finally:
+        if old is None:
+            os.environ.pop("GP_MAKESPAN_KERNEL", None)
+        else:
+            os.environ["GP_MAKESPAN_KERNEL"] = old
+
+
 def test_host_buffers_end_to_end():
     g = FIXTURES["random2k"]()
     with gp.Graph(g) as G:  # numpy inputs: host pointers
