@@ -500,7 +500,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
     StreamFork fork(s);  // the side stream starts here; its kernels are queued after the traversal
     cudaStream_t s2 = fork.side;
-    // ---- topological levels (one thread-block cluster, hardware cluster barrier per level)
+    // ---- topological levels (Kahn: sources, then one CTA while levels are narrow, then one cluster)
     g->lev_vtx = g->own<int32_t>(n, s);
     g->lev_ptr = g->own<int64_t>(n + 2, s);
     g->level = g->own<int32_t>(n, s);
@@ -510,8 +510,21 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     longlong2* frec = A.get<longlong2>(n);
     GP_CUDA(cudaMemsetAsync(tail, 0, 4 * sizeof(unsigned long long), s));
     GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), s));
+    int64_t* resume = A.get<int64_t>(4);  // {level, begin, end, done} where the one-CTA kernel stopped
+    GP_CUDA(cudaMemsetAsync(resume, 0, 4 * sizeof(int64_t), s));
     if (n) {
-      int64_t nn = n;
+      GP_LAUNCH(F_LEVELS, k_levels_init, grid_for(n, 256, 8), 256, 0, s, n, (const int64_t*)g->off,
+                (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->level, tail, frec);
+      if (m < ((int64_t)1 << 31)) {
+        // narrow levels in one CTA: it stops at the first level of more than ~1,300 out-entries (at the
+        // average out-degree), where the cluster kernel's ~3.5 us per level becomes the cheaper one
+        const double deg = (double)m / (double)n;
+        int64_t mw = (int64_t)(1300.0 / (deg > 1.0 ? deg : 1.0));
+        mw = mw < 32 ? 32 : (mw > 4096 ? 4096 : mw);
+        GP_CUDA(cudaFuncSetAttribute(k_levels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevCtaSmem));
+        GP_LAUNCH(F_LEVELS, k_levels_cta, 1, 1024, kLevCtaSmem, s, n, (const int64_t*)g->off, (const int32_t*)g->cols,
+                  rem, g->lev_vtx, g->lev_ptr, g->level, tail, nlev_dev, frec, resume, mw);
+      }
       const int G = makespan_group(n, m);
       int ok = 0;
       switch (G) {
@@ -519,9 +532,9 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
   case GG: {                                                                                            \
     const int cs = cluster_max((const void*)k_levels<GG>, 1024, 0);                                     \
     if (cs > 0) {                                                                                       \
-      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, s, nn, (const int64_t*)g->off,         \
-                             (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->lev_ptr, \
-                             g->level, tail, nlev_dev, frec));                                          \
+      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, s, (const int64_t*)g->off,             \
+                             (const int32_t*)g->cols, rem, g->lev_vtx, g->lev_ptr, g->level, tail, nlev_dev, \
+                             frec, (const int64_t*)resume));                                            \
       ok = 1;                                                                                           \
     }                                                                                                   \
   } break;

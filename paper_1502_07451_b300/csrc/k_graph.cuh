@@ -73,25 +73,24 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Kahn's algorithm, level-synchronous, in one thread-block cluster.  Level l holds the vertices
-// whose longest path from a source has l edges: lev_vtx[lev_ptr[l] .. lev_ptr[l+1]).  A group of G
-// lanes expands one frontier vertex.  New frontier vertices of level l+1 are appended after the
-// current level with counter cnt[(l+1) % 3]; the counter of level l+2 is cleared during level l, after
-// every thread has read it as the size of level l-1, so one barrier per level suffices.
-// cnt[3] receives the number of vertices placed (n exactly when the graph is acyclic).
-template <int G>
-__global__ void __launch_bounds__(1024)
-    k_levels(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
-             const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int64_t* lev_ptr,
-             int32_t* level, unsigned long long* cnt, int32_t* nlev_out, longlong2* frec) {
-  __shared__ unsigned long long sacc[32];
+// Kahn's algorithm, level-synchronous.  Level l holds the vertices whose longest path from a source
+// has l edges: lev_vtx[lev_ptr[l] .. lev_ptr[l+1]).  Every placed vertex also gets a frontier record
+// frec[pos] = (row start, vertex << 32 | row length).  Three kernels share the work:
+//   k_levels_init   (grid)      in-degree counters, the sources as level 0, L2 prefetch of the rows;
+//   k_levels_cta    (one CTA)   levels up to max_width vertices, one __syncthreads() per level (one SM
+//                               issues every gather and counter decrement of a level, so it only
+//                               pays on narrow levels: the host sets max_width to about 1,300
+//                               out-entries' worth of vertices);
+//   k_levels        (cluster)   resumes where the CTA kernel stopped (a wider level), if it did.
+// New frontier vertices of level l+1 are appended after level l with counter cnt[(l+1) % 3]; the
+// counter of level l+2 is cleared during level l, after every thread has read it as the size of level
+// l-1, so one barrier per level suffices.  cnt[3] receives the number of vertices placed (n exactly
+// when the graph is acyclic).  resume = {level, begin, end, done}.
+__global__ void k_levels_init(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                              const int64_t* __restrict__ in_off, int32_t* rem, int32_t* lev_vtx, int32_t* level,
+                              unsigned long long* cnt, longlong2* frec) {
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t group = tid / G, ngroups = stride / G;
-  const int sub = (int)(tid % G);
-  // algorithmic bytes: per vertex its in-range (16), counter init (4), frontier slot (4), row range
-  // (16), level-order slot and level (8); per out-entry the id (4) and the counter decrement (8)
-  unsigned long long bytes = 0;
   prefetch_l2(off, sizeof(int64_t) * (size_t)(n + 1));  // the level loop chases these: keep them in L2
   prefetch_l2(cols, sizeof(int32_t) * (size_t)off[n]);
   for (int64_t v = tid; v < n; v += stride) {
@@ -101,13 +100,159 @@ __global__ void __launch_bounds__(1024)
       const unsigned long long pos = atomicAdd(&cnt[0], 1ull);
       lev_vtx[pos] = (int32_t)v;
       level[v] = 0;
-      // frontier record: row start, (vertex << 32 | row length)
       frec[pos] = make_longlong2(off[v], ((long long)v << 32) | (long long)(off[v + 1] - off[v]));
     }
   }
-  cluster_sync();
-  int64_t beg = 0, end = (int64_t) * (volatile unsigned long long*)&cnt[0];
+}
+
+constexpr int kLevCap = 4096;            // frontier records of a level kept in shared memory
+constexpr int kLevK = 8;                 // out-entries per lane in flight
+constexpr size_t kLevCtaSmem = 2 * kLevCap * sizeof(longlong2);
+
+// One CTA of 1,024 threads; requires m < 2^31.  A warp takes 32 frontier vertices, and its lanes split
+// their out-entries evenly (a lane's share is contiguous in the concatenation of the 32 rows), kLevK
+// at a time: the column ids are loaded together, then the counter decrements are issued together with
+// the loads of the successors' row ranges, so that a level costs two dependent round trips.
+__global__ void __launch_bounds__(1024, 1)
+    k_levels_cta(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols, int32_t* rem,
+                 int32_t* lev_vtx, int64_t* lev_ptr, int32_t* level, unsigned long long* cnt, int32_t* nlev_out,
+                 longlong2* frec, int64_t* resume, int64_t max_width) {
+  extern __shared__ __align__(16) unsigned char lev_smem[];
+  longlong2* buf = (longlong2*)lev_smem;  // [2][kLevCap]
+  __shared__ unsigned int s_cnt[3];
+  __shared__ int32_t s_incl[32][32];
+  __shared__ int32_t s_eb[32][32];
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long bytes = 0;
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0;
+  int64_t beg = 0, end = (int64_t)__ldcg(&cnt[0]);
   int32_t lev = 0;
+  __syncthreads();
+  while (end > beg) {
+    if (end - beg > max_width) {  // uniform: every thread holds the same bounds
+      if (threadIdx.x == 0) {
+        resume[0] = lev;
+        resume[1] = beg;
+        resume[2] = end;
+        resume[3] = 0;
+        cnt[(lev + 1) % 3] = 0;
+        cnt[(lev + 2) % 3] = 0;
+      }
+      account(F_LEVELS, bytes, sacc);
+      return;
+    }
+    if (threadIdx.x == 0) {
+      lev_ptr[lev] = beg;
+      s_cnt[(lev + 2) % 3] = 0;
+    }
+    unsigned int* app = &s_cnt[(lev + 1) % 3];
+    const longlong2* cur = buf + (size_t)(lev & 1) * kLevCap;
+    longlong2* nxt = buf + (size_t)((lev + 1) & 1) * kLevCap;
+    for (int64_t base = beg + (int64_t)warp * 32; base < end; base += 1024) {
+      const int64_t i = base + lane;
+      int32_t eb = 0, len = 0;
+      if (i < end) {
+        const longlong2 rec = (lev > 0 && i - beg < kLevCap) ? cur[i - beg] : __ldcg(frec + i);
+        eb = (int32_t)rec.x;
+        len = (int32_t)(rec.y & 0xFFFFFFFFll);
+        bytes += 48ull + 12ull * (unsigned long long)len;
+      }
+      int32_t incl = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      const int32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      s_incl[warp][lane] = incl;
+      s_eb[warp][lane] = eb;
+      __syncwarp();
+      const int32_t per = (total + 31) >> 5;
+      int32_t k = lane * per < total ? lane * per : total;
+      const int32_t k_end = k + per < total ? k + per : total;
+      // the row holding entry k: first j with incl[j] > k
+      int32_t j = 0;
+      if (k < k_end) {
+        int32_t lo = 0, hi = 31;
+        while (lo < hi) {
+          const int32_t mid = (lo + hi) >> 1;
+          if (s_incl[warp][mid] > k) hi = mid;
+          else lo = mid + 1;
+        }
+        j = lo;
+      }
+      while (k < k_end) {
+        int32_t w[kLevK];
+#pragma unroll
+        for (int q = 0; q < kLevK; q++) {
+          w[q] = -1;
+          if (k < k_end) {
+            while (s_incl[warp][j] <= k) j++;
+            const int32_t excl = j ? s_incl[warp][j - 1] : 0;  // entries of the rows before row j
+            w[q] = cols[s_eb[warp][j] + (k - excl)];
+            k++;
+          }
+        }
+        int32_t r[kLevK], ub[kLevK], ue[kLevK];
+#pragma unroll
+        for (int q = 0; q < kLevK; q++) {
+          r[q] = 0;
+          if (w[q] >= 0) {
+            r[q] = atomicSub(&rem[w[q]], 1);
+            ub[q] = (int32_t)off[w[q]];  // in flight with the decrement
+            ue[q] = (int32_t)off[w[q] + 1];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < kLevK; q++) {
+          if (w[q] >= 0 && r[q] == 1) {
+            const unsigned int a = atomicAdd(app, 1u);
+            const int64_t pos = end + (int64_t)a;
+            const longlong2 rec = make_longlong2((long long)ub[q], ((long long)w[q] << 32) | (long long)(ue[q] - ub[q]));
+            lev_vtx[pos] = w[q];
+            level[w[q]] = lev + 1;
+            frec[pos] = rec;
+            if (a < (unsigned int)kLevCap) nxt[a] = rec;
+            if (ue[q] > ub[q]) asm volatile("prefetch.global.L2 [%0];" ::"l"(cols + ub[q]));
+          }
+        }
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    beg = end;
+    end = beg + (int64_t)*(volatile unsigned int*)app;
+    lev++;
+  }
+  if (threadIdx.x == 0) {
+    lev_ptr[lev] = beg;
+    *nlev_out = lev;
+    cnt[3] = (unsigned long long)beg;
+    resume[3] = 1;
+  }
+  account(F_LEVELS, bytes, sacc);
+}
+
+// The cluster kernel: continues from resume = {level, begin, end, done} (nothing to do when done).
+template <int G>
+__global__ void __launch_bounds__(1024)
+    k_levels(const int64_t* __restrict__ off, const int32_t* __restrict__ cols, int32_t* rem, int32_t* lev_vtx,
+             int64_t* lev_ptr, int32_t* level, unsigned long long* cnt, int32_t* nlev_out, longlong2* frec,
+             const int64_t* resume) {
+  __shared__ unsigned long long sacc[32];
+  if (__ldcg(resume + 3)) return;  // the CTA kernel placed every level
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t group = tid / G, ngroups = stride / G;
+  const int sub = (int)(tid % G);
+  // algorithmic bytes: per vertex its in-range (16), counter init (4), frontier slot (4), row range
+  // (16), level-order slot and level (8); per out-entry the id (4) and the counter decrement (8)
+  unsigned long long bytes = 0;
+  // where the CTA kernel stopped; when it did not run, level 0 as the init kernel left it
+  const int64_t r_end = __ldcg(resume + 2);
+  int64_t beg = __ldcg(resume + 1), end = r_end ? r_end : (int64_t)__ldcg(&cnt[0]);
+  int32_t lev = (int32_t)__ldcg(resume + 0);
   while (end > beg) {
     if (tid == 0) {
       lev_ptr[lev] = beg;
@@ -119,18 +264,25 @@ __global__ void __launch_bounds__(1024)
       const longlong2 rec = __ldcg(frec + i);  // written by other CTAs: bypass L1
       const int64_t eb = rec.x, ee = eb + (rec.y & 0xFFFFFFFFll);
       if (sub == 0) bytes += 48ull + 12ull * (unsigned long long)(ee - eb);
-      // two out-entries per lane at a time: both decrements are in flight together
+      // two out-entries per lane at a time: both decrements are in flight together, and with them the
+      // successors' row ranges (needed by the one whose count reaches zero)
       for (int64_t e = eb + sub; e < ee; e += 2 * G) {
         const bool two = e + G < ee;
         const int32_t u1 = cols[e];
         const int32_t u2 = two ? cols[e + G] : -1;
         const int r1 = atomicSub(&rem[u1], 1);
         const int r2 = two ? atomicSub(&rem[u2], 1) : 0;
+        const int64_t ub1 = off[u1], ue1 = off[u1 + 1];
+        int64_t ub2 = 0, ue2 = 0;
+        if (two) {
+          ub2 = off[u2];
+          ue2 = off[u2 + 1];
+        }
 #pragma unroll
         for (int q = 0; q < 2; q++) {
           const int32_t u = q ? u2 : u1;
           if ((q ? r2 : r1) == 1) {
-            const int64_t ub = off[u], ue = off[u + 1];  // in flight with the append below
+            const int64_t ub = q ? ub2 : ub1, ue = q ? ue2 : ue1;
             // warp-aggregated append: one atomic per set of lanes that got here together
             const unsigned act = __activemask();
             const int lane = threadIdx.x & 31;

@@ -108,6 +108,34 @@ def test_create_is_repeatable():
                 assert np.array_equal(host(lv), lev)
 
 
+def test_levels_from_one_cta_to_the_cluster():
+    """Kahn's levels: narrow levels in one CTA, then a 6,000-wide level where the cluster kernel takes
+    over (its frontier records partly beyond the CTA's shared-memory capacity, read back from global
+    memory), a 10,000-wide level and narrow levels after it; levels, partition and makespan against
+    the oracle."""
+    edges = [(i, i + 1) for i in range(9)]
+    a0, na = 10, 6000
+    c = a0 + na
+    d0, nd = c + 1, 10000
+    e = d0 + nd
+    edges += [(9, a0 + j) for j in range(na)] + [(a0 + j, c) for j in range(na)]
+    edges += [(c, d0 + j) for j in range(nd)] + [(d0 + j, e) for j in range(nd)] + [(e, e + 1), (e + 1, e + 2)]
+    n = e + 3
+    rng = np.random.default_rng(17)
+    g = gen.from_edges(n, edges, rng.integers(1, 1000, n).tolist(), rng.integers(1, 1000, n).tolist(),
+                       rng.integers(1, 100, len(edges)).tolist())
+    lev, nl = oracle.levels(g)
+    with gp.Graph(dgraph(g)) as G:
+        assert G.info()["nlevels"] == nl == 16
+        lv = torch.empty(n, dtype=torch.int32, device="cuda")
+        gp.gp_graph_export(G.h, level=lv)
+        assert np.array_equal(host(lv), lev)
+    part, res, tr, ms = gpu_partition(g, seed=2)
+    opart, ores = oracle.partition(g, seed=2)
+    assert np.array_equal(part, opart) and {k: res[k] for k in ores} == ores
+    assert ms == oracle.makespan(g, opart)
+
+
 def test_long_rows_use_every_merge_tier():
     """Rows of <= 256 (warp), <= 8192 (block) and > 8192 raw entries (radix tier), with parallel edges."""
     k = 20000
