@@ -767,8 +767,29 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     cand.dirty[0] = A.get<int32_t>(n);
     cand.dirty[1] = A.get<int32_t>(n);
     GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
-    for (int l = Lc; l >= 0; l--) {
-      if (l < Lc) {
+    // the coarse levels (at most kTailMaxVertices vertices each) in one CTA launch, then the rest level
+    // by level over the whole grid
+    int lo = Lc + 1;
+    while (lo - 1 >= 0 && L[lo - 1].n <= kTailMaxVertices && Lc - (lo - 1) + 1 <= kTailMaxLevels) lo--;
+    if (lo <= Lc) {
+      TailArgs ta;
+      memset(&ta, 0, sizeof(ta));
+      ta.lo = lo;
+      ta.hi = Lc;
+      for (int l = Lc; l >= lo; l--) {
+        if (l < Lc) parts[l] = A.get<uint8_t>(L[l].n);
+        TailLevel& t = ta.lev[l - lo];
+        t.g = L[l];
+        t.cmap = l < Lc ? cmaps[l] : nullptr;
+        t.part = parts[l];
+        t.G = group_for_degree((double)T.a[l] / (double)(T.n[l] > 0 ? T.n[l] : 1));
+        t.idbits = idbits_for(L[l].n);
+      }
+      GP_LAUNCH(F_SELECT, k_refine_tail, 1, 1024, 0, s, ta, &td->ctl, cand, td->rounds, td->moves, td->bal,
+                td->balmoves);
+    }
+    for (int l = lo - 1; l >= 0; l--) {
+      if (l < Lc) {  // the coarsest level holds the growing's split
         parts[l] = A.get<uint8_t>(L[l].n);
         project(L[l].n, cmaps[l], parts[l + 1], parts[l], s);
       }
