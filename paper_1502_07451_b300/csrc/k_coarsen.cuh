@@ -180,7 +180,7 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
 template <int G>
 __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* __restrict__ mate,
                              int32_t* __restrict__ anchor, uint8_t* __restrict__ is_anchor, int64_t tid,
-                             int64_t stride) {
+                             int64_t stride, int32_t* __restrict__ scnt = nullptr) {
   __shared__ unsigned long long sacc[32];
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
@@ -221,7 +221,8 @@ __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* 
       } else {
         const int32_t a = key_other(best, (uint32_t)v);
         anchor[v] = a;
-        is_anchor[a] = 1;
+        if (is_anchor) is_anchor[a] = 1;
+        if (scnt) atomicAdd(&scnt[a], 1);  // the anchor's bucket size
       }
     }
   }
@@ -230,9 +231,19 @@ __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* 
 template <int G>
 __global__ void __launch_bounds__(256)
     k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
-             uint8_t* __restrict__ is_anchor) {
+             uint8_t* __restrict__ is_anchor, int32_t* __restrict__ scnt) {
   match_anchor<G>(g, seed, mate, anchor, is_anchor, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                  (int64_t)gridDim.x * blockDim.x);
+                  (int64_t)gridDim.x * blockDim.x, scnt);
+}
+
+// every anchored vertex into its anchor's bucket: sat[soff[a] .. soff[a + 1]) (in no particular order;
+// scnt, the bucket sizes, counts down to zero)
+__global__ void k_sat_scatter(int64_t n, const int32_t* __restrict__ anchor, const int64_t* __restrict__ soff,
+                              int32_t* __restrict__ scnt, int32_t* __restrict__ sat) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = anchor[v];
+    if (a >= 0) sat[soff[a] + atomicSub(&scnt[a], 1) - 1] = (int32_t)v;
+  }
 }
 
 // Pairs the vertices anchored at h in ascending vertex order.  Sequentially: a vertex joins the
@@ -442,26 +453,61 @@ __device__ void twohop_warps(const LevelGraph& g, int64_t capC, int64_t capG, co
     }
   }
 }
+// Warp per anchor, from the anchors' buckets: loads its bucket, sorts it and pairs it (the pairing of
+// twohop_warps, which finds the same vertices by scanning the anchor's row).  Buckets of more than
+// kSatCap go to the list `big`.
 __global__ void __launch_bounds__(kTwohopWarps * 32)
-    k_twohop(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
-             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate, int32_t* __restrict__ big,
-             unsigned* big_cnt, int nbits) {
-  __shared__ int32_t sat[kTwohopWarps][2][kSatCap];
+    k_twohop_b(LevelGraph g, int64_t capC, int64_t capG, const int64_t* __restrict__ soff,
+               const int32_t* __restrict__ sat, int32_t* __restrict__ mate, int32_t* __restrict__ big,
+               unsigned* big_cnt, int nbits) {
+  __shared__ int32_t sbuf[kTwohopWarps][2][kSatCap];
   __shared__ int hist_all[kTwohopWarps][256];
   __shared__ unsigned long long sacc[32];
-  const int wib = threadIdx.x >> 5;
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * kTwohopWarps + wib, nw = (int64_t)gridDim.x * kTwohopWarps;
+  int32_t* S = sbuf[wib][0];
   unsigned long long bytes = 0;
-  twohop_warps(g, capC, capG, anchor, is_anchor, mate, big, big_cnt, nbits, (int64_t)blockIdx.x * kTwohopWarps + wib,
-               (int64_t)gridDim.x * kTwohopWarps, sat[wib][0], sat[wib][1], hist_all[wib], kSatCap, bytes);
+  for (int64_t hb = gw * 32; hb < g.n; hb += nw * 32) {
+    const int64_t h0 = hb + lane;
+    const int64_t lo = h0 < g.n ? soff[h0] : 0, hi = h0 < g.n ? soff[h0 + 1] : 0;
+    unsigned am = __ballot_sync(0xffffffffu, hi > lo);
+    while (am) {
+      const int src = __ffs(am) - 1;
+      am &= am - 1;
+      const int64_t h = hb + src;
+      const int64_t b = __shfl_sync(0xffffffffu, lo, src);
+      const int k = (int)(__shfl_sync(0xffffffffu, hi, src) - b);
+      if (k > kSatCap) {
+        if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
+        continue;
+      }
+      for (int q = lane; q < k; q += 32) S[q] = sat[b + q];
+      bytes += 4ull * (unsigned long long)k;
+      __syncwarp();
+      const int32_t* sorted = S;
+      if (k <= 32) {
+        const int32_t x = warp_sort32(lane < k ? S[lane] : INT32_MAX, lane);
+        __syncwarp();
+        S[lane] = x;
+        __syncwarp();
+      } else {
+        sorted = warp_radix_keys(S, sbuf[wib][1], k, nbits, hist_all[wib]);
+      }
+      pair_sorted(g, capC, capG, sorted, k, mate, bytes);
+      __syncwarp();
+    }
+  }
   account(F_TWOHOP, bytes, sacc);
 }
 
 // Block per anchor with more than kSatCap anchored vertices: gather them into scratch (the anchor's
-// row region), LSD radix sort by vertex id (8-bit digits), then one warp pairs them.
+// row region, or its bucket when soff is given), LSD radix sort by vertex id (8-bit digits), then one
+// warp pairs them.
 __global__ void __launch_bounds__(1024)
     k_twohop_big(LevelGraph g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
                  int32_t* __restrict__ mate, const int32_t* __restrict__ big, const unsigned* big_cnt,
-                 int32_t* __restrict__ ta, int32_t* __restrict__ tb, int nbits) {
+                 int32_t* __restrict__ ta, int32_t* __restrict__ tb, int nbits,
+                 const int64_t* __restrict__ soff = nullptr, const int32_t* __restrict__ sat = nullptr) {
   __shared__ unsigned s_k;
   __shared__ unsigned hist[256];
   __shared__ unsigned binbase[256];
@@ -473,13 +519,17 @@ __global__ void __launch_bounds__(1024)
   const unsigned nbig = *big_cnt;
   for (unsigned bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
     const int32_t h = big[bi];
-    const int64_t b = g.start[h];
-    const int32_t d = g.deg[h];
-    if (threadIdx.x == 0) s_k = 0;
+    const int64_t b = soff ? soff[h] : g.start[h];
+    const int32_t d = soff ? (int32_t)(soff[h + 1] - b) : g.deg[h];
+    if (threadIdx.x == 0) s_k = soff ? (unsigned)d : 0u;
     __syncthreads();
-    for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {
-      const int32_t v = g.adj[b + q];
-      if (anchor[v] == h) ta[b + atomicAdd(&s_k, 1u)] = v;
+    if (soff) {
+      for (int32_t q = threadIdx.x; q < d; q += blockDim.x) ta[b + q] = sat[b + q];
+    } else {
+      for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {
+        const int32_t v = g.adj[b + q];
+        if (anchor[v] == h) ta[b + atomicAdd(&s_k, 1u)] = v;
+      }
     }
     __syncthreads();
     const int64_t N = s_k;
@@ -616,28 +666,40 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
     GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick);
   }
   if (twohop) {
+    // every unmatched vertex into the bucket of its anchor (count, scan, scatter), then a warp per
+    // anchor pairs its bucket; buckets of more than kSatCap vertices, a block each
     int32_t* anchor = pick;  // reuse
-    uint8_t* is_anchor = alive;
+    int32_t* scnt = dnew<int32_t>(n, s);
+    int64_t* soff = dnew<int64_t>(n + 1, s);
+    int32_t* sat = dnew<int32_t>(n, s);
     unsigned* big_cnt = dnew<unsigned>(1, s);
     int32_t* big = dnew<int32_t>(n, s);
-    int32_t* ta = dnew<int32_t>(g.cap, s);
-    int32_t* tb = dnew<int32_t>(g.cap, s);
-    GP_CUDA(cudaMemsetAsync(is_anchor, 0, (size_t)n, s));
+    int32_t* ta = dnew<int32_t>(n, s);
+    int32_t* tb = dnew<int32_t>(n, s);
+    GP_CUDA(cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (size_t)n, s));
     GP_CUDA(cudaMemsetAsync(big_cnt, 0, sizeof(unsigned), s));
     switch (G) {
 #define GP_AN(GG)                                                                                         \
   case GG:                                                                                               \
-    GP_LAUNCH(F_TWOHOP, k_anchor<GG>, grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor, is_anchor); \
+    GP_LAUNCH(F_TWOHOP, k_anchor<GG>, grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor,             \
+              (uint8_t*)nullptr, scnt);                                                                  \
     break;
       GP_AN(2) GP_AN(4) GP_AN(8) GP_AN(16) GP_AN(32)
 #undef GP_AN
     }
+    scan_i32_to_i64(scnt, soff, n, s);
+    GP_LAUNCH(F_TWOHOP, k_sat_scatter, grid_for(n, 256), 256, 0, s, n, (const int32_t*)anchor,
+              (const int64_t*)soff, scnt, sat);
     int nbits = 1;
     while (nbits < 31 && (int64_t(1) << nbits) < n) nbits++;
-    GP_LAUNCH(F_TWOHOP, k_twohop, grid_for(n, kTwohopWarps * 32, 16), kTwohopWarps * 32, 0, s, g, capC, capG,
-              anchor, is_anchor, mate, big, big_cnt, nbits);
-    GP_LAUNCH(F_TWOHOP, k_twohop_big, (unsigned)num_sms(), 1024, 0, s, g, capC, capG, anchor, mate, big, big_cnt,
-              ta, tb, nbits);
+    GP_LAUNCH(F_TWOHOP, k_twohop_b, grid_for(n, kTwohopWarps * 32, 16), kTwohopWarps * 32, 0, s, g, capC, capG,
+              (const int64_t*)soff, (const int32_t*)sat, mate, big, big_cnt, nbits);
+    GP_LAUNCH(F_TWOHOP, k_twohop_big, (unsigned)num_sms(), 1024, 0, s, g, capC, capG, (const int32_t*)anchor, mate,
+              (const int32_t*)big, (const unsigned*)big_cnt, ta, tb, nbits, (const int64_t*)soff,
+              (const int32_t*)sat);
+    dfree(scnt, s);
+    dfree(soff, s);
+    dfree(sat, s);
     dfree(big_cnt, s);
     dfree(big, s);
     dfree(ta, s);
