@@ -77,9 +77,11 @@ class BatchGen:
         return self.held.get()
 
     def wait(self):
-        """Block until every graph is built (no worker competes with the timed regions)."""
+        """Block until every graph is built, then end the workers (their results stay with the
+        parent), so that no worker process competes with the timed regions."""
         self.res.wait()
         self.held.wait()
+        self.close()
 
     def graphs(self):
         out = [None] * self.count
@@ -89,8 +91,10 @@ class BatchGen:
         return out
 
     def close(self):
-        self.pool.close()
-        self.pool.join()
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
 
 
 def profiled_traffic(family):
