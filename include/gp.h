@@ -94,6 +94,24 @@ GP_API gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, c
                           const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
                           int ptr_kind, void* stream, gp_graph** out);
 
+/* ---------------------------------------------------------------------------------------------
+ * gp_graph_create_deferred -- gp_graph_create that returns once the undirected graph is built: the
+ * topological levels and the level-ordered in-CSR (which only the makespan, the learned proposal's
+ * features and the level export read) are computed on a second stream of the device, on the few
+ * SMs a level traversal occupies, while the caller goes on (e.g. with gp_partition, which does not
+ * need them).  Arguments as gp_graph_create; the caller must not modify or free the input arrays
+ * before the call returns (they are copied).
+ * Errors at creation: GP_ERR_INVALID, GP_ERR_OVERFLOW, GP_ERR_NOT_DAG for a self-loop, GP_ERR_OOM,
+ * GP_ERR_CUDA.  A cycle through more than one vertex is reported as GP_ERR_NOT_DAG by the first call
+ * that waits for the levels: gp_partition (after its split is written), gp_makespan,
+ * gp_makespan_noalloc, gp_graph_info (with nlevels), gp_graph_export (with level), the network and
+ * learned entry points and the batch entry points; each of them waits for the levels once, and
+ * returns the same status for that handle from then on.  gp_graph_destroy waits for them too.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_graph_create_deferred(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                                   const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                                   int ptr_kind, void* stream, gp_graph** out);
+
 GP_API gp_status gp_graph_destroy(gp_graph* g);
 
 /* ---------------------------------------------------------------------------------------------

@@ -78,6 +78,7 @@ def lib():
             L = C.CDLL(path)
             sig = {
                 "gp_graph_create": [_I64, _I64, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)],
+                "gp_graph_create_deferred": [_I64, _I64, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)],
                 "gp_graph_destroy": [_P],
                 "gp_graph_info": [_P, _P, _P, _P, _P, _P, _P],
                 "gp_graph_export": [_P, _P, _P, _P, _P, _P],
@@ -183,18 +184,28 @@ def _stream(stream):
 # C-ABI, same names
 # ---------------------------------------------------------------------------
 
-def gp_graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, stream=None):
-    """Copy a DAG (out-CSR + costs) to the device and validate it; returns the handle."""
-    arrs = [offsets, cols, edge_cost, cpu_cost, gpu_cost]
+def _create(fn, name, n, m, arrs, stream):
     ptrs = [_ptr(a) for a in arrs]
     kinds = {dev for (_, dev) in ptrs}
     if len(kinds) != 1:
         raise ValueError("all five arrays must live on the same side (host or device)")
     h = _P()
-    st = lib().gp_graph_create(int(n), int(m), *[p for p, _ in ptrs], 1 if kinds.pop() else 0, _stream(stream),
-                               C.byref(h))
-    _check(st, "gp_graph_create")
+    st = fn(int(n), int(m), *[p for p, _ in ptrs], 1 if kinds.pop() else 0, _stream(stream), C.byref(h))
+    _check(st, name)
     return h
+
+
+def gp_graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, stream=None):
+    """Copy a DAG (out-CSR + costs) to the device and validate it; returns the handle."""
+    return _create(lib().gp_graph_create, "gp_graph_create", n, m, [offsets, cols, edge_cost, cpu_cost, gpu_cost],
+                   stream)
+
+
+def gp_graph_create_deferred(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, stream=None):
+    """gp_graph_create whose topological levels are computed beside the caller's next work; a cycle
+    is reported (GP_ERR_NOT_DAG) by the first call that needs the levels."""
+    return _create(lib().gp_graph_create_deferred, "gp_graph_create_deferred", n, m,
+                   [offsets, cols, edge_cost, cpu_cost, gpu_cost], stream)
 
 
 def gp_graph_create_batch(graphs, stream=None):
@@ -504,10 +515,11 @@ def kernel_families():
 class Graph:
     """Device copy of a DAG given as a dict of arrays (see gen.py), torch or numpy."""
 
-    def __init__(self, g, stream=None):
+    def __init__(self, g, stream=None, deferred=False):
         self.n, self.m = int(g["n"]), int(g["m"])
-        self.h = gp_graph_create(self.n, self.m, g["offsets"], g["cols"], g["edge_cost"], g["cpu_cost"],
-                                 g["gpu_cost"], stream=stream)
+        create = gp_graph_create_deferred if deferred else gp_graph_create
+        self.h = create(self.n, self.m, g["offsets"], g["cols"], g["edge_cost"], g["cpu_cost"], g["gpu_cost"],
+                        stream=stream)
 
     def info(self):
         return gp_graph_info(self.h)

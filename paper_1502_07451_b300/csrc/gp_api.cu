@@ -227,6 +227,7 @@ struct StreamFork {
     cudaEventRecord(ev, side);
     cudaStreamWaitEvent(main, ev, 0);
   }
+  void detach() { joined = true; }  // the side stream's work goes on; the main stream does not wait
   ~StreamFork() {
     join();
     if (ev) cudaEventDestroy(ev);
@@ -299,6 +300,14 @@ struct gp_graph {
   int32_t* in_src = nullptr;
   int32_t* in_w = nullptr;
   bool in_sorted = false;     // in-rows sorted by (source, cost): set before the network first reads them
+  // deferred levels (gp_graph_create_deferred): the level traversal and the level-ordered in-CSR run on
+  // a side stream after creation returns; lev_event marks their end, lev_host receives {vertices
+  // placed, levels, widest level}, and levels_ready() waits for them once
+  bool lev_pending = false;
+  gp_status lev_status = GP_OK;
+  cudaEvent_t lev_event = nullptr;
+  int64_t* lev_host = nullptr;  // pinned slot of 4 int64
+  std::mutex lev_mu;
   std::shared_ptr<void> block;  // device block shared by the handles of one gp_graph_create_batch call
   LevelGraph L0;
   gp_trace trace;
@@ -311,12 +320,54 @@ struct gp_graph {
   }
 };
 
+// Pinned host slots of 4 int64 (carved from 64 KiB pinned chunks, recycled): targets of the deferred
+// level results' device-to-host copies, so that creating a graph allocates no pinned memory.
+static std::mutex g_slot_mu;
+static std::vector<int64_t*> g_slot_free;
+static int64_t* pinned_slot_alloc() {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if (g_slot_free.empty()) {
+    void* chunk = nullptr;
+    if (cudaMallocHost(&chunk, 65536) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = 0; i < 65536 / 32; i++) g_slot_free.push_back((int64_t*)chunk + 4 * i);
+  }
+  int64_t* p = g_slot_free.back();
+  g_slot_free.pop_back();
+  return p;
+}
+static void pinned_slot_free(int64_t* p) {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  g_slot_free.push_back(p);
+}
+
+// Waits (once) for a deferred creation's level work and takes its results: GP_ERR_NOT_DAG when the
+// traversal placed fewer than n vertices (a cycle).  A no-op for a graph created without deferral.
+static gp_status levels_ready(const gp_graph* cg) {
+  gp_graph* g = const_cast<gp_graph*>(cg);
+  std::lock_guard<std::mutex> lk(g->lev_mu);
+  if (!g->lev_pending) return g->lev_status;
+  if (cudaEventSynchronize(g->lev_event) != cudaSuccess) {
+    cudaGetLastError();
+    return GP_ERR_CUDA;
+  }
+  g->nlev = (int32_t)g->lev_host[1];
+  g->max_width = g->lev_host[2];
+  g->lev_status = g->lev_host[0] == g->n ? GP_OK : GP_ERR_NOT_DAG;
+  g->lev_pending = false;
+  return g->lev_status;
+}
+
 static void graph_free(gp_graph* g) {
   if (!g) return;
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(g->dev);
-  cudaDeviceSynchronize();
+  cudaDeviceSynchronize();  // includes deferred level work on the side stream
+  if (g->lev_event) cudaEventDestroy(g->lev_event);
+  if (g->lev_host) pinned_slot_free(g->lev_host);
   for (void* p : g->owned) cudaFree(p);
   g->block.reset();  // the shared block is freed with its last handle
   cudaSetDevice(cur);
@@ -418,9 +469,13 @@ gp_status gp_bounds(int64_t sum_cpu, int64_t sum_gpu, double r_cpu, double tol, 
   return host_bounds(sum_cpu, sum_gpu, r_cpu, tol, bound_cpu, bound_gpu);
 }
 
-gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
-                          const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
-                          int ptr_kind, void* stream, gp_graph** out) {
+}  // extern "C"
+
+// Graph creation.  deferred: the level traversal and the level-ordered in-CSR run on the side stream
+// and creation returns once the symmetrised graph is built (levels_ready() collects them).
+static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                              const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                              int ptr_kind, void* stream, gp_graph** out, bool deferred) {
   if (!out) return GP_ERR_INVALID;
   *out = nullptr;
   if (n < 0 || m < 0 || n > kMaxN || (ptr_kind != 0 && ptr_kind != 1)) return GP_ERR_INVALID;
@@ -484,8 +539,8 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
                      indeg, in_src, in_w, flags);
     GP_CHECK_LAUNCH();
     // ---- symmetrisation: row v = out-row(v) + in-row(v), merged (Sec. III.B: one cost per transfer).
-    // It needs only the two CSRs, so it runs on a second stream while the level traversal (one cluster
-    // of SMs) runs on the first.
+    // It needs only the two CSRs, so it runs on one stream while the level traversal (one cluster of
+    // SMs) runs on another: the side stream takes the symmetrisation, or with deferral the levels.
     LevelGraph& L = g->L0;
     L.n = n;
     L.cap = 2 * m;
@@ -498,22 +553,38 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     int64_t* rawlen = A.get<int64_t>(n);
     unsigned long long* a0 = A.get<unsigned long long>(1);
     GP_CUDA(cudaMemsetAsync(a0, 0, sizeof(unsigned long long), s));
-    StreamFork fork(s);  // the side stream starts here; its kernels are queued after the traversal
-    cudaStream_t s2 = fork.side;
-    // ---- topological levels (Kahn: sources, then one CTA while levels are narrow, then one cluster)
     g->lev_vtx = g->own<int32_t>(n, s);
     g->lev_ptr = g->own<int64_t>(n + 2, s);
     g->level = g->own<int32_t>(n, s);
-    int32_t* rem = A.get<int32_t>(n);
-    unsigned long long* tail = A.get<unsigned long long>(4);  // 3 rotating level counters + total
-    int32_t* nlev_dev = A.get<int32_t>(1);
-    longlong2* frec = A.get<longlong2>(n);
-    GP_CUDA(cudaMemsetAsync(tail, 0, 4 * sizeof(unsigned long long), s));
-    GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), s));
-    int64_t* resume = A.get<int64_t>(4);  // {level, begin, end, done} where the one-CTA kernel stopped
-    GP_CUDA(cudaMemsetAsync(resume, 0, 4 * sizeof(int64_t), s));
+    g->lo_off = g->own<int64_t>(n + 1, s);
+    g->lo_src = g->own<int32_t>(m, s);
+    g->lo_w = g->own<int32_t>(m, s);
+    g->lo_cC = g->own<int32_t>(n, s);
+    g->lo_cG = g->own<int32_t>(n, s);
+    if (deferred && n) {
+      // unplaced positions of a cyclic graph must read as -1 in the level-ordered in-CSR build
+      GP_CUDA(cudaMemsetAsync(g->lev_vtx, 0xff, sizeof(int32_t) * n, s));
+      g->lev_host = pinned_slot_alloc();
+      if (!g->lev_host || cudaEventCreateWithFlags(&g->lev_event, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        throw Fail{GP_ERR_CUDA};
+      }
+    }
+    StreamFork fork(s);  // the side stream starts here, after everything above
+    const cudaStream_t sl = deferred ? fork.side : s;  // the levels
+    const cudaStream_t ss = deferred ? s : fork.side;  // the symmetrisation
+    Arena AL(sl);  // temporaries of the level work, freed in its stream's order
+    // ---- topological levels (Kahn: sources, then one CTA while levels are narrow, then one cluster)
+    int32_t* rem = AL.get<int32_t>(n);
+    unsigned long long* tail = AL.get<unsigned long long>(4);  // 3 rotating level counters + total
+    int32_t* nlev_dev = AL.get<int32_t>(1);
+    longlong2* frec = AL.get<longlong2>(n);
+    GP_CUDA(cudaMemsetAsync(tail, 0, 4 * sizeof(unsigned long long), sl));
+    GP_CUDA(cudaMemsetAsync(nlev_dev, 0, sizeof(int32_t), sl));
+    int64_t* resume = AL.get<int64_t>(4);  // {level, begin, end, done} where the one-CTA kernel stopped
+    GP_CUDA(cudaMemsetAsync(resume, 0, 4 * sizeof(int64_t), sl));
     if (n) {
-      GP_LAUNCH(F_LEVELS, k_levels_init, grid_for(n, 256, 8), 256, 0, s, n, (const int64_t*)g->off,
+      GP_LAUNCH(F_LEVELS, k_levels_init, grid_for(n, 256, 8), 256, 0, sl, n, (const int64_t*)g->off,
                 (const int32_t*)g->cols, (const int64_t*)in_off, rem, g->lev_vtx, g->level, tail, frec);
       if (m < ((int64_t)1 << 31)) {
         // narrow levels in one CTA: it stops at the first level of more than ~1,300 out-entries (at the
@@ -522,8 +593,8 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
         int64_t mw = (int64_t)(1300.0 / (deg > 1.0 ? deg : 1.0));
         mw = mw < 32 ? 32 : (mw > 4096 ? 4096 : mw);
         GP_CUDA(cudaFuncSetAttribute(k_levels_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLevCtaSmem));
-        GP_LAUNCH(F_LEVELS, k_levels_cta, 1, 1024, kLevCtaSmem, s, n, (const int64_t*)g->off, (const int32_t*)g->cols,
-                  rem, g->lev_vtx, g->lev_ptr, g->level, tail, nlev_dev, frec, resume, mw);
+        GP_LAUNCH(F_LEVELS, k_levels_cta, 1, 1024, kLevCtaSmem, sl, n, (const int64_t*)g->off,
+                  (const int32_t*)g->cols, rem, g->lev_vtx, g->lev_ptr, g->level, tail, nlev_dev, frec, resume, mw);
       }
       const int G = makespan_group(n, m);
       int ok = 0;
@@ -532,7 +603,7 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
   case GG: {                                                                                            \
     const int cs = cluster_max((const void*)k_levels<GG>, 1024, 0);                                     \
     if (cs > 0) {                                                                                       \
-      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, s, (const int64_t*)g->off,             \
+      GP_CUDA(launch_cluster(F_LEVELS, k_levels<GG>, cs, 1024, 0, sl, (const int64_t*)g->off,            \
                              (const int32_t*)g->cols, rem, g->lev_vtx, g->lev_ptr, g->level, tail, nlev_dev, \
                              frec, (const int64_t*)resume));                                            \
       ok = 1;                                                                                           \
@@ -543,12 +614,12 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
       }
       if (!ok) throw Fail{GP_ERR_CUDA};
     }
-    // the symmetrisation, on the side stream, beside the traversal
+    // the symmetrisation, beside the traversal
     if (n) {
-      GP_LAUNCH(F_SYM_MERGE, k_rawlen_sym, grid_for(n, 256), 256, 0, s2, n, g->off, in_off, rawlen);
-      GP_LAUNCH(F_MISC, k_widen, grid_for(n, 256), 256, 0, s2, n, g->cC, g->cG, L.vC, L.vG);
+      GP_LAUNCH(F_SYM_MERGE, k_rawlen_sym, grid_for(n, 256), 256, 0, ss, n, g->off, in_off, rawlen);
+      GP_LAUNCH(F_MISC, k_widen, grid_for(n, 256), 256, 0, ss, n, g->cC, g->cG, L.vC, L.vG);
     }
-    scan_i64(rawlen, L.start, n, s2);
+    scan_i64(rawlen, L.start, n, ss);
     {
       TwoSrc src{};
       src.a_start = g->off;
@@ -558,42 +629,54 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
       src.b_col = in_src;
       src.b_w32 = in_w;
       src.drop_self = 0;
-      merge_rows_unordered(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, s2);
+      merge_rows_unordered(src, n, n, L.start, L.deg, L.adj, L.W, F_SYM_MERGE, 2 * m, ss);
     }
-    if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, s2, n, L.deg, a0);
+    if (n) GP_LAUNCH(F_MISC, k_sum_deg, grid_for(n, 256, 8), 256, 0, ss, n, L.deg, a0);
     GP_CHECK_LAUNCH();
-    unsigned long long htail = 0;
-    int32_t hnlev = 0;
-    GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(&htail, tail + 3, sizeof(htail), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaMemcpyAsync(&hnlev, nlev_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    GP_CUDA(cudaStreamSynchronize(s));
-    if ((hflags & VF_SELFLOOP) || (n > 0 && (int64_t)htail != n)) throw Fail{GP_ERR_NOT_DAG};
-    g->nlev = hnlev;
-    {
-      std::vector<int64_t> lp((size_t)hnlev + 1);
-      if (n) GP_CUDA(cudaMemcpy(lp.data(), g->lev_ptr, sizeof(int64_t) * (hnlev + 1), cudaMemcpyDeviceToHost));
-      int64_t mw = 0;
-      for (int l = 0; l < hnlev; l++) mw = std::max(mw, lp[l + 1] - lp[l]);
-      g->max_width = mw;
+    // ---- level-ordered in-CSR for the makespan (after the traversal, on its stream); its inputs
+    // are the traversal's positions, which exist whether or not the graph turns out acyclic
+    auto lo_csr = [&]() {
+      int32_t* pos_of = AL.get<int32_t>(n);
+      int32_t* lo_deg = AL.get<int32_t>(n);
+      if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_prep, grid_for(n, 256), 256, 0, sl, n, g->lev_vtx, in_off, g->cC, g->cG,
+                       pos_of, lo_deg, g->lo_cC, g->lo_cG);
+      scan_i32_to_i64(lo_deg, g->lo_off, n, sl);
+      if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_fill, grid_for(n * 32, 256), 256, 0, sl, n, g->lev_vtx, in_off, in_src,
+                       in_w, pos_of, g->lo_off, g->lo_src, g->lo_w);
+    };
+    if (!deferred) {
+      unsigned long long htail = 0;
+      int32_t hnlev = 0;
+      GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaMemcpyAsync(&htail, tail + 3, sizeof(htail), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaMemcpyAsync(&hnlev, nlev_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      if ((hflags & VF_SELFLOOP) || (n > 0 && (int64_t)htail != n)) throw Fail{GP_ERR_NOT_DAG};
+      g->nlev = hnlev;
+      {
+        std::vector<int64_t> lp((size_t)hnlev + 1);
+        if (n) GP_CUDA(cudaMemcpy(lp.data(), g->lev_ptr, sizeof(int64_t) * (hnlev + 1), cudaMemcpyDeviceToHost));
+        int64_t mw = 0;
+        for (int l = 0; l < hnlev; l++) mw = std::max(mw, lp[l + 1] - lp[l]);
+        g->max_width = mw;
+      }
+      lo_csr();
+      fork.join();  // the first stream waits for the symmetrisation
+    } else if (n) {
+      // the traversal's results, read by levels_ready(): vertices placed, levels, widest level
+      lo_csr();
+      int64_t* res3 = AL.get<int64_t>(3);
+      GP_LAUNCH(F_MISC, k_level_summary, 1, 256, 0, sl, tail + 3, nlev_dev, (const int64_t*)g->lev_ptr, res3);
+      GP_CUDA(cudaMemcpyAsync(g->lev_host, res3, 3 * sizeof(int64_t), cudaMemcpyDeviceToHost, sl));
+      GP_CUDA(cudaEventRecord(g->lev_event, sl));
+      g->lev_pending = true;
+      fork.detach();
     }
-    // ---- level-ordered in-CSR for the makespan
-    int32_t* pos_of = A.get<int32_t>(n);
-    int32_t* lo_deg = A.get<int32_t>(n);
-    g->lo_off = g->own<int64_t>(n + 1, s);
-    g->lo_src = g->own<int32_t>(m, s);
-    g->lo_w = g->own<int32_t>(m, s);
-    g->lo_cC = g->own<int32_t>(n, s);
-    g->lo_cG = g->own<int32_t>(n, s);
-    if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_prep, grid_for(n, 256), 256, 0, s, n, g->lev_vtx, in_off, g->cC, g->cG, pos_of,
-                     lo_deg, g->lo_cC, g->lo_cG);
-    scan_i32_to_i64(lo_deg, g->lo_off, n, s);
-    if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_fill, grid_for(n * 32, 256), 256, 0, s, n, g->lev_vtx, in_off, in_src, in_w,
-                     pos_of, g->lo_off, g->lo_src, g->lo_w);
-    fork.join();  // the first stream waits for the symmetrisation
     unsigned long long ha0 = 0;
     GP_CUDA(cudaMemcpyAsync(&ha0, a0, sizeof(ha0), cudaMemcpyDeviceToHost, s));
+    if (deferred) GP_CUDA(cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
+    if (deferred && (hflags & VF_SELFLOOP)) throw Fail{GP_ERR_NOT_DAG};
     g->a0 = (int64_t)ha0;
     *out = g;
     return GP_OK;
@@ -602,6 +685,20 @@ gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const in
     graph_free(g);
     return f.st;
   }
+}
+
+extern "C" {
+
+gp_status gp_graph_create(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                          const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                          int ptr_kind, void* stream, gp_graph** out) {
+  return graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, ptr_kind, stream, out, false);
+}
+
+gp_status gp_graph_create_deferred(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                                   const int32_t* edge_cost, const int32_t* cpu_cost, const int32_t* gpu_cost,
+                                   int ptr_kind, void* stream, gp_graph** out) {
+  return graph_create(n, m, offsets, cols, edge_cost, cpu_cost, gpu_cost, ptr_kind, stream, out, true);
 }
 
 gp_status gp_graph_destroy(gp_graph* g) {
@@ -613,6 +710,10 @@ gp_status gp_graph_destroy(gp_graph* g) {
 gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* m, int64_t* a0, int32_t* nlevels, int64_t* sum_cpu,
                         int64_t* sum_gpu) {
   if (!g) return GP_ERR_INVALID;
+  if (nlevels) {
+    const gp_status ls = levels_ready(g);
+    if (ls != GP_OK) return ls;
+  }
   if (n) *n = g->n;
   if (m) *m = g->m;
   if (a0) *a0 = g->a0;
@@ -624,6 +725,10 @@ gp_status gp_graph_info(const gp_graph* g, int64_t* n, int64_t* m, int64_t* a0, 
 
 gp_status gp_graph_export(const gp_graph* g, int64_t* off, int32_t* adj, int64_t* W, int32_t* level, void* stream) {
   if (!g) return GP_ERR_INVALID;
+  if (level) {
+    const gp_status ls = levels_ready(g);
+    if (ls != GP_OK) return ls;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   try {
     Arena A(s);
@@ -827,7 +932,7 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     }
     g->trace = T;
     if (res) *res = R;
-    return GP_OK;
+    return levels_ready(g);  // a deferred creation's cycle check (its traversal ran beside this call)
   } catch (Fail& f) {
     cudaGetLastError();
     return f.st;
@@ -874,6 +979,10 @@ gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* str
 
 gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan, int64_t* finish_out, void* stream) {
   if (!g || !makespan || (!part && g->n > 0)) return GP_ERR_INVALID;
+  {
+    const gp_status ls = levels_ready(g);
+    if (ls != GP_OK) return ls;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = g->n;
   if (n == 0) {

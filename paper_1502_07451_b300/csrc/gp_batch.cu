@@ -277,6 +277,11 @@ static gp_status batch_run(int32_t count, gp_graph* const* graphs, const double*
   if (count == 0) return GP_OK;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GP_ERR_CUDA;
+  for (int i = 0; i < count; i++)
+    if (graphs[i]) {
+      const gp_status ls = levels_ready(graphs[i]);  // the makespans read the levels
+      if (ls != GP_OK) return ls;
+    }
   std::vector<BatchJob> kjobs, direct;
   std::vector<int64_t> BCs(count), BGs(count);
   size_t stage = 0;

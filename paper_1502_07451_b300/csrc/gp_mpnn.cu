@@ -180,6 +180,8 @@ static void mp_prepare(const gp_graph* gc, cudaStream_t s) {
 }
 
 static MpGraph mp_graph(const gp_graph* g) {
+  const gp_status ls = levels_ready(g);  // the features read the levels
+  if (ls != GP_OK) throw Fail{ls};
   MpGraph G;
   G.n = g->n;
   G.m = g->m;
@@ -652,6 +654,10 @@ static float* mp_union_logits(const gp_model* M, gp_graph* const* graphs, const 
   int64_t N = 0, Mtot = 0;
   base.assign(K, 0);
   int32_t maxlev = 0;
+  for (int i = 0; i < K; i++) {
+    const gp_status ls = levels_ready(graphs[sel[i]]);  // the features read the levels
+    if (ls != GP_OK) throw Fail{ls};
+  }
   for (int i = 0; i < K; i++) mp_prepare(graphs[sel[i]], s);
   for (int i = 0; i < K; i++) {
     const gp_graph* g = graphs[sel[i]];

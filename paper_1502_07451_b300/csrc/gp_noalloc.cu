@@ -53,6 +53,10 @@ extern "C" gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part,
     *makespan = 0;
     return GP_OK;
   }
+  {
+    const gp_status ls = levels_ready(g);  // a deferred creation's levels (allocates nothing)
+    if (ls != GP_OK) return ls;
+  }
   // no staging copies here: the mapping and the finish times must already be device memory
   if (!is_device_ptr(part) || (finish_out && !is_device_ptr(finish_out))) return GP_ERR_INVALID;
   unsigned long long* base = nullptr;

@@ -311,13 +311,46 @@ __global__ void __launch_bounds__(1024)
   account(F_LEVELS, bytes, sacc);
 }
 
-// position i of the level order: vertex, in-degree, costs
+// {vertices placed, levels, widest level} of a traversal (one block)
+__global__ void k_level_summary(const unsigned long long* placed, const int32_t* nlev, const int64_t* lev_ptr,
+                                int64_t* out) {
+  __shared__ long long sh[32];
+  const int32_t L = *nlev;
+  long long mw = 0;
+  for (int32_t l = threadIdx.x; l < L; l += blockDim.x) {
+    const long long w = lev_ptr[l + 1] - lev_ptr[l];
+    mw = w > mw ? w : mw;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long q = __shfl_xor_sync(0xffffffffu, mw, o);
+    mw = q > mw ? q : mw;
+  }
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mw;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = sh[w] > m ? sh[w] : m;
+    out[0] = (int64_t)*placed;
+    out[1] = L;
+    out[2] = m;
+  }
+}
+
+// position i of the level order: vertex, in-degree, costs (positions a cyclic graph left unplaced hold
+// -1 when the level order was cleared first, and get no entries)
 __global__ void k_lo_prep(int64_t n, const int32_t* __restrict__ lev_vtx, const int64_t* __restrict__ in_off,
                           const int32_t* __restrict__ cC, const int32_t* __restrict__ cG,
                           int32_t* __restrict__ pos_of, int32_t* __restrict__ lo_deg,
                           int32_t* __restrict__ lo_cC, int32_t* __restrict__ lo_cG) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = lev_vtx[i];
+    if (v < 0) {
+      lo_deg[i] = 0;
+      lo_cC[i] = 0;
+      lo_cG[i] = 0;
+      continue;
+    }
     pos_of[v] = (int32_t)i;
     lo_deg[i] = (int32_t)(in_off[v + 1] - in_off[v]);
     lo_cC[i] = cC[v];
@@ -335,6 +368,7 @@ __global__ void __launch_bounds__(256)
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n; i += nw) {
     const int32_t v = lev_vtx[i];
+    if (v < 0) continue;  // unplaced (cyclic graph): no entries
     const int64_t b = in_off[v], d = in_off[v + 1] - b, o = lo_off[i];
     for (int64_t k = lane; k < d; k += 32) {
       lo_src[o + k] = pos_of[in_src[b + k]];
