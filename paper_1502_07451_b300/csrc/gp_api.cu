@@ -812,17 +812,38 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     const int64_t capC = BC / kCapDiv, capG = BG / kCapDiv;
     TraceDev* td = A.get<TraceDev>(1);
     GP_CUDA(cudaMemsetAsync(td, 0, sizeof(TraceDev), s));
-    unsigned long long* adev = A.get<unsigned long long>(1);
+    // entries of each coarse level, summed on the device and read with the next level's vertex count
+    // (one host round trip per level); until then a level's kernels size their lane groups from the
+    // bound the fine level gives (c.cap), which changes no result
+    unsigned long long* adev = A.get<unsigned long long>(kMaxLevels + 2);
+    GP_CUDA(cudaMemsetAsync(adev, 0, sizeof(unsigned long long) * (kMaxLevels + 2), s));
+    int64_t* hbuf = pinned_slot_alloc();  // [0]: the coarse vertex count (int32), [1]: entries
+    if (!hbuf) throw Fail{GP_ERR_OOM};
+    struct SlotGuard {
+      int64_t* p;
+      ~SlotGuard() { pinned_slot_free(p); }
+    } slot_guard{hbuf};
     int lev = 0;
+    auto take_entries = [&](int l) {  // level l's entries, copied to hbuf[1] before the last sync
+      L[l].a = hbuf[1];
+      T.a[l] = hbuf[1];
+    };
+    bool pending_a = false;  // L[lev].a still to be taken from hbuf[1]
     while (L[lev].n > kCoarsest && lev < kMaxLevels) {
       const LevelGraph& f = L[lev];
       int32_t* mate = dnew<int32_t>(f.n, s);
       int32_t* cmap = A.get<int32_t>(f.n + 1);
       match_level(f, capC, capG, seed, kMatchRounds, true, mate, s);
       coarse_count(f, mate, cmap, nullptr, s);
-      int32_t nc = 0;
-      GP_CUDA(cudaMemcpyAsync(&nc, cmap + f.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      int32_t* hnc = (int32_t*)&hbuf[0];
+      GP_CUDA(cudaMemcpyAsync(hnc, cmap + f.n, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      if (pending_a) GP_CUDA(cudaMemcpyAsync(&hbuf[1], adev + lev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       GP_CUDA(cudaStreamSynchronize(s));
+      const int32_t nc = *hnc;
+      if (pending_a) {
+        take_entries(lev);
+        pending_a = false;
+      }
       if ((int64_t)nc * kStallDen > f.n * kStallNum) {
         dfree(mate, s);
         break;
@@ -838,17 +859,18 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
       A.ptrs.push_back(c.W);
       A.ptrs.push_back(c.vC);
       A.ptrs.push_back(c.vG);
-      GP_CUDA(cudaMemsetAsync(adev, 0, sizeof(unsigned long long), s));
-      GP_LAUNCH(F_MISC, k_sum_deg, grid_for(nc, 256, 8), 256, 0, s, (int64_t)nc, c.deg, adev);
-      unsigned long long ha = 0;
-      GP_CUDA(cudaMemcpyAsync(&ha, adev, sizeof(ha), cudaMemcpyDeviceToHost, s));
-      GP_CUDA(cudaStreamSynchronize(s));
+      GP_LAUNCH(F_MISC, k_sum_deg, grid_for(nc, 256, 8), 256, 0, s, (int64_t)nc, c.deg, adev + lev + 1);
       cmaps.push_back(cmap);
-      c.a = (int64_t)ha;
+      c.a = 0;  // taken at the next level's round trip
       L.push_back(c);
       lev++;
       T.n[lev] = nc;
-      T.a[lev] = (int64_t)ha;
+      pending_a = true;
+    }
+    if (pending_a) {  // the coarsest level's entries
+      GP_CUDA(cudaMemcpyAsync(&hbuf[1], adev + lev, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      take_entries(lev);
     }
     const int Lc = lev;
     if (prof) cudaEventRecord(ev[1], s);
