@@ -197,18 +197,43 @@ __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part,
   const int64_t* csrc = src == 0 ? g.vC : g.vG;
   unsigned long long sum_cd = 0, sum_cs = 0, bytes = 0;
   long long gmax = LLONG_MIN, gmin = LLONG_MAX;
-  for (int64_t v = tid; v < g.n; v += stride) {
-    bytes += 1;
-    if (part[v] != src) continue;
-    bytes += 12;
-    if (cand.stamp[v] == prev_tag) continue;  // stale: recomputed below
-    const long long gain = cand.gainv[v];
-    if (r < 0 || gain > 0) {
-      push_cand(cc, cand, (int32_t)v, gain, cdst[v], csrc[v], sum_cd, sum_cs, gmax, gmin);
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  // whole warps step together (v = warp base + lane), so that a warp reserves its candidates' slots
+  // with one atomic
+  for (int64_t vb = tid - lane; vb < g.n; vb += stride) {
+    const int64_t v = vb + lane;
+    bool want = false;
+    long long gain = 0;
+    if (v < g.n) {
+      bytes += 1;
+      if (part[v] == src) {
+        bytes += 12;
+        if (cand.stamp[v] != prev_tag) {  // stale ones are recomputed below
+          gain = cand.gainv[v];
+          want = r < 0 || gain > 0;
+        }
+      }
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) continue;
+    unsigned long long slot0 = 0;
+    if (lane == __ffs(m) - 1) slot0 = atomicAdd(&cc->ncand, (unsigned long long)__popc(m));
+    slot0 = __shfl_sync(0xffffffffu, slot0, __ffs(m) - 1);
+    if (want) {
+      const unsigned long long slot = slot0 + __popc(m & lt);
+      const long long cdv = cdst[v], csv = csrc[v];
+      cand.id[slot] = (int32_t)v;
+      cand.gain[slot] = gain;
+      cand.cd[slot] = cdv;
+      cand.cs[slot] = csv;
+      sum_cd += (unsigned long long)cdv;
+      sum_cs += (unsigned long long)csv;
+      gmax = gain > gmax ? gain : gmax;
+      gmin = gain < gmin ? gain : gmin;
       bytes += 44;
     }
   }
-  const int lane = threadIdx.x & 31;
   const int32_t* dl = cand.dirty[(r < 0) ? 0 : (r & 1)];
   for (int64_t k = tid >> 5; k < (int64_t)s_nd; k += stride >> 5) {
     const int32_t v = dl[k];
@@ -450,6 +475,7 @@ __device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restr
   const int dst = 1 - s_src;
   const u128 thr = ((u128)s_hi << 64) | (u128)s_lo;
   const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
   unsigned long long* nd = &ctl->ndirty[(r + 1) & 1];
   int32_t* dl = cand.dirty[(r + 1) & 1];
   long long dC = 0, dG = 0;
@@ -474,9 +500,20 @@ __device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restr
     }
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
-    for (int32_t q = lane; q < d; q += 32) {
-      const int32_t u = g.adj[b + q];
-      if (atomicExch(&cand.stamp[u], tag) != tag) dl[atomicAdd(nd, 1ull)] = u;
+    for (int32_t qb = 0; qb < d; qb += 32) {  // the warp reserves its new stale entries with one atomic
+      const int32_t q = qb + lane;
+      int32_t u = -1;
+      bool fresh = false;
+      if (q < d) {
+        u = g.adj[b + q];
+        fresh = atomicExch(&cand.stamp[u], tag) != tag;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, fresh);
+      if (!m) continue;
+      unsigned long long p0 = 0;
+      if (lane == __ffs(m) - 1) p0 = atomicAdd(nd, (unsigned long long)__popc(m));
+      p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
+      if (fresh) dl[p0 + __popc(m & lt)] = u;
     }
     if (lane == 0) bytes += 12ull + 8ull * (unsigned long long)d;
   }
