@@ -24,6 +24,11 @@ static const SchedDef kSched[] = {
     {512, 2, {1, 256}, "cta512x2_wide_rows"},
     {512, 2, {-1, 256}, "cta512x2_narrow_rows"},
     {512, 2, {0, 128}, "cta512x2_hash128"},
+    {512, 2, {-2, 256}, "cta512x2_quarter_rows"},
+    {512, 2, {-3, 256}, "cta512x2_eighth_rows"},
+    {512, 2, {-4, 256}, "cta512x2_sixteenth_rows"},
+    {256, 4, {-1, 256}, "cta256x4_narrow_rows"},
+    {256, 4, {-2, 256}, "cta256x4_quarter_rows"},
 };
 constexpr int kNumSched = (int)(sizeof(kSched) / sizeof(kSched[0]));
 
