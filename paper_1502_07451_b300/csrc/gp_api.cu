@@ -894,26 +894,42 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     cand.dirty[0] = A.get<int32_t>(n);
     cand.dirty[1] = A.get<int32_t>(n);
     GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
-    // the coarse levels (at most kTailMaxVertices vertices each) in one CTA launch, then the rest level
-    // by level over the whole grid
-    int lo = Lc + 1;
-    while (lo - 1 >= 0 && L[lo - 1].n <= kTailMaxVertices && Lc - (lo - 1) + 1 <= kTailMaxLevels) lo--;
-    if (lo <= Lc) {
+    // the coarse levels (at most kTailMaxVertices vertices each) in one CTA launch, the next ones (up to
+    // kClusterTailMaxVertices) in one cluster launch, then the rest level by level over the whole grid
+    auto tail_args = [&](int a, int b, double gscale) {  // levels b (coarser) down to a
       TailArgs ta;
       memset(&ta, 0, sizeof(ta));
-      ta.lo = lo;
-      ta.hi = Lc;
-      for (int l = Lc; l >= lo; l--) {
+      ta.lo = a;
+      ta.hi = b;
+      ta.top_part = b < Lc ? parts[b + 1] : nullptr;
+      for (int l = b; l >= a; l--) {
         if (l < Lc) parts[l] = A.get<uint8_t>(L[l].n);
-        TailLevel& t = ta.lev[l - lo];
+        TailLevel& t = ta.lev[l - a];
         t.g = L[l];
         t.cmap = l < Lc ? cmaps[l] : nullptr;
         t.part = parts[l];
-        t.G = group_for_degree((double)T.a[l] / (double)(T.n[l] > 0 ? T.n[l] : 1));
+        t.G = group_for_degree(gscale * (double)T.a[l] / (double)(T.n[l] > 0 ? T.n[l] : 1));
         t.idbits = idbits_for(L[l].n);
       }
-      GP_LAUNCH(F_SELECT, k_refine_tail, 1, 1024, 0, s, ta, &td->ctl, cand, td->rounds, td->moves, td->bal,
+      return ta;
+    };
+    int lo = Lc + 1;
+    while (lo - 1 >= 0 && L[lo - 1].n <= kTailMaxVertices && Lc - (lo - 1) + 1 <= kTailMaxLevels) lo--;
+    if (lo <= Lc) {
+      const TailArgs ta = tail_args(lo, Lc, 1.0);
+      GP_LAUNCH(F_SELECT, k_refine_tail<false>, 1, 1024, 0, s, ta, &td->ctl, cand, td->rounds, td->moves, td->bal,
                 td->balmoves);
+    }
+    {
+      int lo2 = lo;
+      while (lo2 - 1 >= 0 && L[lo2 - 1].n <= kClusterTailMaxVertices && lo - (lo2 - 1) <= kTailMaxLevels) lo2--;
+      const int cs = lo2 < lo ? cluster_max((const void*)k_refine_tail<true>, 1024, 0) : 0;
+      if (lo2 < lo && cs > 0) {
+        const TailArgs ta = tail_args(lo2, lo - 1, 0.25);
+        GP_CUDA(launch_cluster(F_SELECT, k_refine_tail<true>, cs, 1024, 0, s, ta, &td->ctl, cand, td->rounds,
+                               td->moves, td->bal, td->balmoves));
+        lo = lo2;
+      }
     }
     for (int l = lo - 1; l >= 0; l--) {
       if (l < Lc) {  // the coarsest level holds the growing's split

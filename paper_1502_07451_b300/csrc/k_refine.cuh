@@ -578,6 +578,8 @@ static inline int group_for_degree(double avg) {
 // record written.  Replaces ~31 launches per level where the levels are small.
 constexpr int kTailMaxLevels = 48;
 constexpr int64_t kTailMaxVertices = 4096;  // measured on the 1M workload: 2,048-4,096 best (12.56 vs 13.07 ms)
+constexpr int64_t kClusterTailMaxVertices = 16384;  // one cluster up to here (1M workload: 10.95 -> 10.81 ms;
+                                                     // 65,536 measured slower, 11.26 ms)
 struct TailLevel {
   LevelGraph g;
   const int32_t* cmap;  // level l -> level l + 1 (unused at hi)
@@ -587,47 +589,63 @@ struct TailLevel {
 };
 struct TailArgs {
   int32_t lo, hi;
+  const uint8_t* top_part;        // split of level hi + 1, projected onto level hi (null: hi is the coarsest)
   TailLevel lev[kTailMaxLevels];  // lev[l - lo]
 };
 
+// CLUSTER: the same over one thread-block cluster (the cluster's threads share each step, the cluster
+// barrier separates the steps, the one-block selection runs in rank 0), for levels a little larger.
+template <bool CLUSTER>
 __global__ void __launch_bounds__(1024, 1)
     k_refine_tail(TailArgs A, Ctl* ctl, Cands cand, int32_t* t_rounds, long long* t_moves, int32_t* t_bal,
                   long long* t_balmoves) {
+  uint32_t rank = 0, nranks = 1;
+  if (CLUSTER) {
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nranks));
+  }
+  const int64_t tid = (int64_t)rank * blockDim.x + threadIdx.x, stride = (int64_t)nranks * blockDim.x;
+  const bool lead = rank == 0 && threadIdx.x == 0;
+  auto sync = [&]() {
+    if (CLUSTER)
+      cluster_sync();
+    else
+      __syncthreads();
+  };
   for (int l = A.hi; l >= A.lo; l--) {
     const TailLevel& T = A.lev[l - A.lo];
     const LevelGraph& g = T.g;
-    if (l < A.hi) {
-      const uint8_t* pc = A.lev[l + 1 - A.lo].part;
-      for (int64_t v = threadIdx.x; v < g.n; v += blockDim.x) T.part[v] = pc[T.cmap[v]];
-    }
-    if (threadIdx.x == 0) ref_begin(ctl, T.idbits);
-    __syncthreads();
+    const uint8_t* pc = l < A.hi ? A.lev[l + 1 - A.lo].part : A.top_part;
+    if (pc)
+      for (int64_t v = tid; v < g.n; v += stride) T.part[v] = pc[T.cmap[v]];
+    if (lead) ref_begin(ctl, T.idbits);
+    sync();
     switch (T.G) {
-      case 2: gain_all<2>(g, T.part, cand.gainv, threadIdx.x, blockDim.x); break;
-      case 4: gain_all<4>(g, T.part, cand.gainv, threadIdx.x, blockDim.x); break;
-      case 8: gain_all<8>(g, T.part, cand.gainv, threadIdx.x, blockDim.x); break;
-      case 16: gain_all<16>(g, T.part, cand.gainv, threadIdx.x, blockDim.x); break;
-      default: gain_all<32>(g, T.part, cand.gainv, threadIdx.x, blockDim.x); break;
+      case 2: gain_all<2>(g, T.part, cand.gainv, tid, stride); break;
+      case 4: gain_all<4>(g, T.part, cand.gainv, tid, stride); break;
+      case 8: gain_all<8>(g, T.part, cand.gainv, tid, stride); break;
+      case 16: gain_all<16>(g, T.part, cand.gainv, tid, stride); break;
+      default: gain_all<32>(g, T.part, cand.gainv, tid, stride); break;
     }
-    __syncthreads();
+    sync();
     int32_t prev = round_tag(l, -2);
     for (int r = -1; r < kRefineRounds; r++) {
-      ref_cands(g, T.part, ctl, r, prev, cand, threadIdx.x, blockDim.x);
-      __syncthreads();
-      ref_select(ctl, r, cand);
-      __syncthreads();
-      ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, threadIdx.x, blockDim.x);
-      __syncthreads();
+      ref_cands(g, T.part, ctl, r, prev, cand, tid, stride);
+      sync();
+      if (rank == 0) ref_select(ctl, r, cand);
+      sync();
+      ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, tid, stride);
+      sync();
       prev = round_tag(l, r);
-      if (*(volatile int32_t*)&ctl->done) break;  // later rounds would return at once
+      if (*(volatile int32_t*)&ctl->done) break;  // later rounds would return at once (uniform: read after the barrier)
     }
-    if (threadIdx.x == 0) {
+    if (lead) {
       t_rounds[l] = ctl->rounds;
       t_moves[l] = ctl->moves;
       t_bal[l] = ctl->balanced;
       t_balmoves[l] = ctl->bal_moves;
     }
-    __syncthreads();
+    sync();
   }
 }
 
