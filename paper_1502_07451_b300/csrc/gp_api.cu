@@ -273,6 +273,18 @@ static int makespan_group(int64_t n, int64_t m) {
   return 32;
 }
 
+// the cut of a mapping over the directed out-CSR (G lanes per row from the average out-degree)
+static void launch_cut(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                       const uint8_t* part, unsigned long long* cut, int* bad, cudaStream_t s) {
+  if (n <= 0) return;
+  switch (makespan_group(n, m)) {
+#define GP_CUTG(GG) \
+  case GG: GP_LAUNCH(F_CUT, k_cut<GG>, grid_for(n * GG, 256), 256, 0, s, n, off, cols, w, part, cut, bad); break;
+    GP_CUTG(2) GP_CUTG(4) GP_CUTG(8) GP_CUTG(16) GP_CUTG(32)
+#undef GP_CUTG
+  }
+}
+
 }  // namespace gp
 
 using namespace gp;
@@ -940,7 +952,7 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
       GP_LAUNCH(F_MISC, k_ref_end, 1, 1, 0, s, &td->ctl, l, td->rounds, td->moves, td->bal, td->balmoves);
     }
     if (prof) cudaEventRecord(ev[3], s);
-    GP_LAUNCH(F_CUT, k_cut, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, parts[0], &td->cut, &td->bad);
+    launch_cut(n, g->m, g->off, g->cols, g->w, parts[0], &td->cut, &td->bad, s);
     GP_CHECK_LAUNCH();
     GP_CUDA(cudaMemcpyAsync(part_out, parts[0], (size_t)n, cudaMemcpyDefault, s));
     if (prof) cudaEventRecord(ev[4], s);
@@ -999,7 +1011,7 @@ gp_status gp_cut(const gp_graph* g, const uint8_t* part, int64_t* cut, void* str
     int* bad = A.get<int>(1);
     GP_CUDA(cudaMemsetAsync(c, 0, sizeof(unsigned long long), s));
     GP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    if (n) GP_LAUNCH(F_CUT, k_cut, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, p, c, bad);
+    launch_cut(n, g->m, g->off, g->cols, g->w, p, c, bad, s);
     GP_CHECK_LAUNCH();
     unsigned long long hc = 0;
     int hb = 0;

@@ -610,7 +610,7 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
     int* bad = A.get<int>(1);
     GP_CUDA(cudaMemsetAsync(cut, 0, sizeof(unsigned long long), s));
     GP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
-    GP_LAUNCH(F_CUT, k_cut, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, part, cut, bad);
+    launch_cut(n, g->m, g->off, g->cols, g->w, part, cut, bad, s);
     GP_CHECK_LAUNCH();
     GP_CUDA(cudaMemcpyAsync(part_out, part, (size_t)n, cudaMemcpyDefault, s));
     if (prof) cudaEventRecord(ev[3], s);

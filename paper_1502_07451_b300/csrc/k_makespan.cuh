@@ -135,24 +135,26 @@ __global__ void __launch_bounds__(1024)
   account(F_MAKESPAN, bytes, sacc);
 }
 
-// cut over the directed out-CSR (warp per row)
+// cut over the directed out-CSR: a group of G lanes per row (G from the average out-degree, about one
+// entry per lane), so that a warp has 32 / G rows' loads in flight
+template <int G>
 __global__ void __launch_bounds__(256)
     k_cut(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
           const int32_t* __restrict__ w, const uint8_t* __restrict__ part, unsigned long long* cut,
           int* bad_part) {
   __shared__ unsigned long long sh[32];
   __shared__ unsigned long long sacc[32];
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t group = tid / G, ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int sub = threadIdx.x % G;
   unsigned long long s = 0, bytes = 0;
-  for (int64_t u = gw; u < n; u += nw) {
+  for (int64_t u = group; u < n; u += ngroups) {
     const uint8_t pu = part[u];
-    if (pu > 1 && lane == 0) atomicOr(bad_part, 1);
+    if (pu > 1 && sub == 0) atomicOr(bad_part, 1);
     const int64_t b = off[u], e_end = off[u + 1];
-    for (int64_t e = b + lane; e < e_end; e += 32)
+    for (int64_t e = b + sub; e < e_end; e += G)
       if (part[cols[e]] != pu) s += (unsigned long long)w[e];
-    if (lane == 0) bytes += 17ull + (unsigned long long)(e_end - b) * 9ull;
+    if (sub == 0) bytes += 17ull + (unsigned long long)(e_end - b) * 9ull;
   }
   s = block_sum<unsigned long long>(s, sh);
   if (threadIdx.x == 0 && s) atomicAdd(cut, s);
