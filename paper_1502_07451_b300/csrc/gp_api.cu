@@ -547,8 +547,17 @@ static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, cons
     if (m) GP_LAUNCH(F_TRANSPOSE, k_indeg, grid_for(m, 256, 8), 256, 0, s, m, g->cols, indeg);
     scan_i32_to_i64(indeg, in_off, n, s);
     GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));  // reused as fill cursor
-    if (n) GP_LAUNCH(F_TRANSPOSE, k_fill_in, grid_for(n * 32, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off,
-                     indeg, in_src, in_w, flags);
+    if (n) {
+      switch (makespan_group(n, m)) {  // lanes per row from the average out-degree
+#define GP_FI(GG)                                                                                           \
+  case GG:                                                                                                  \
+    GP_LAUNCH(F_TRANSPOSE, k_fill_in<GG>, grid_for(n * GG, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off, \
+              indeg, in_src, in_w, flags);                                                                  \
+    break;
+        GP_FI(2) GP_FI(4) GP_FI(8) GP_FI(16) GP_FI(32)
+#undef GP_FI
+      }
+    }
     GP_CHECK_LAUNCH();
     // ---- symmetrisation: row v = out-row(v) + in-row(v), merged (Sec. III.B: one cost per transfer).
     // It needs only the two CSRs, so it runs on one stream while the level traversal (one cluster of
@@ -653,8 +662,17 @@ static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, cons
       if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_prep, grid_for(n, 256), 256, 0, sl, n, g->lev_vtx, in_off, g->cC, g->cG,
                        pos_of, lo_deg, g->lo_cC, g->lo_cG);
       scan_i32_to_i64(lo_deg, g->lo_off, n, sl);
-      if (n) GP_LAUNCH(F_TRANSPOSE, k_lo_fill, grid_for(n * 32, 256), 256, 0, sl, n, g->lev_vtx, in_off, in_src,
-                       in_w, pos_of, g->lo_off, g->lo_src, g->lo_w);
+      if (n) {
+        switch (makespan_group(n, m)) {  // lanes per position from the average in-degree
+#define GP_LF(GG)                                                                                          \
+  case GG:                                                                                                 \
+    GP_LAUNCH(F_TRANSPOSE, k_lo_fill<GG>, grid_for(n * GG, 256), 256, 0, sl, n, g->lev_vtx, in_off, in_src,  \
+              in_w, pos_of, g->lo_off, g->lo_src, g->lo_w);                                                \
+    break;
+          GP_LF(2) GP_LF(4) GP_LF(8) GP_LF(16) GP_LF(32)
+#undef GP_LF
+        }
+      }
     };
     if (!deferred) {
       unsigned long long htail = 0;

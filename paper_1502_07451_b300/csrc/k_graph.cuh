@@ -54,16 +54,17 @@ __global__ void k_indeg(int64_t m, const int32_t* __restrict__ cols, int32_t* __
 }
 
 // in-CSR fill (warp per source row); also detects self-loops
+template <int G>  // lanes per row
 __global__ void __launch_bounds__(256)
     k_fill_in(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
               const int32_t* __restrict__ w, const int64_t* __restrict__ in_off, int32_t* cursor,
               int32_t* __restrict__ in_src, int32_t* __restrict__ in_w, int* flags) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sub = threadIdx.x % G;
+  const int64_t gw = tid / G, nw = ((int64_t)gridDim.x * blockDim.x) / G;
   for (int64_t u = gw; u < n; u += nw) {
     const int64_t b = off[u], e_end = off[u + 1];
-    for (int64_t e = b + lane; e < e_end; e += 32) {
+    for (int64_t e = b + sub; e < e_end; e += G) {
       const int32_t v = cols[e];
       if (v == (int32_t)u) atomicOr(flags, VF_SELFLOOP);
       const int64_t pos = in_off[v] + atomicAdd(&cursor[v], 1);
@@ -358,19 +359,20 @@ __global__ void k_lo_prep(int64_t n, const int32_t* __restrict__ lev_vtx, const 
   }
 }
 
+template <int G>  // lanes per position
 __global__ void __launch_bounds__(256)
     k_lo_fill(int64_t n, const int32_t* __restrict__ lev_vtx, const int64_t* __restrict__ in_off,
               const int32_t* __restrict__ in_src, const int32_t* __restrict__ in_w,
               const int32_t* __restrict__ pos_of, const int64_t* __restrict__ lo_off,
               int32_t* __restrict__ lo_src, int32_t* __restrict__ lo_w) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int sub = threadIdx.x % G;
+  const int64_t gw = tid / G, nw = ((int64_t)gridDim.x * blockDim.x) / G;
   for (int64_t i = gw; i < n; i += nw) {
     const int32_t v = lev_vtx[i];
     if (v < 0) continue;  // unplaced (cyclic graph): no entries
     const int64_t b = in_off[v], d = in_off[v + 1] - b, o = lo_off[i];
-    for (int64_t k = lane; k < d; k += 32) {
+    for (int64_t k = sub; k < d; k += G) {
       lo_src[o + k] = pos_of[in_src[b + k]];
       lo_w[o + k] = in_w[b + k];
     }
