@@ -483,6 +483,85 @@ __global__ void __launch_bounds__(WARPS * 32)
   account(fam, bytes, sacc);
 }
 
+// Warp per row of at most 32 raw entries, without a table: each lane holds one entry, __match_any_sync
+// finds the lanes holding the same column, and the lowest of them sums their weights and writes the
+// merged entry (at its rank among those lowest lanes).  Longer rows go to the list of their tier.
+__global__ void __launch_bounds__(256)
+    k_merge_match(TwoSrc s, int64_t nrows, const int64_t* __restrict__ out_start, int32_t* __restrict__ deg_out,
+                  int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int32_t* __restrict__ dl1,
+                  unsigned* dc1, int64_t split1, int32_t* __restrict__ dl2, unsigned* dc2, int64_t split2,
+                  int32_t* __restrict__ dl3, unsigned* dc3, int64_t split3, int32_t* __restrict__ dl4,
+                  unsigned* dc4, int fam) {
+  __shared__ unsigned long long sacc[32];
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = lanemask_lt();
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long bytes = 0;
+  // 32 rows per warp step: every lane measures one row, the long ones go to their tier's list with one
+  // atomic per tier and step, then the warp merges the short ones one after another
+  for (int64_t rb = gw * 32; rb < nrows; rb += nw * 32) {
+    const int64_t rl = rb + lane;
+    RowView mv{0, 0, 0, 0};
+    int64_t mlen = -1;
+    if (rl < nrows) {
+      mv = row_view(s, rl);
+      mlen = mv.a_len + mv.b_len;
+    }
+    const int tier = mlen < 0 ? -1 : mlen <= 32 ? 0 : mlen <= split1 ? 1 : mlen <= split2 ? 2 : mlen <= split3 ? 3 : 4;
+#pragma unroll
+    for (int t = 1; t <= 4; t++) {
+      const unsigned m = __ballot_sync(0xffffffffu, tier == t);
+      if (!m) continue;
+      int32_t* dl = t == 1 ? dl1 : t == 2 ? dl2 : t == 3 ? dl3 : dl4;
+      unsigned* dc = t == 1 ? dc1 : t == 2 ? dc2 : t == 3 ? dc3 : dc4;
+      unsigned p0 = 0;
+      if (lane == __ffs(m) - 1) p0 = atomicAdd(dc, (unsigned)__popc(m));
+      p0 = __shfl_sync(0xffffffffu, p0, __ffs(m) - 1);
+      if (tier == t) dl[p0 + __popc(m & lt)] = (int32_t)rl;
+    }
+    for (unsigned sm = __ballot_sync(0xffffffffu, tier == 0); sm; sm &= sm - 1) {
+      const int src = __ffs(sm) - 1;
+      const int64_t r = rb + src;
+      RowView v;
+      v.a_beg = __shfl_sync(0xffffffffu, mv.a_beg, src);
+      v.a_len = __shfl_sync(0xffffffffu, mv.a_len, src);
+      v.b_beg = __shfl_sync(0xffffffffu, mv.b_beg, src);
+      v.b_len = __shfl_sync(0xffffffffu, mv.b_len, src);
+      const int64_t len = v.a_len + v.b_len;
+      int32_t col = -1;
+      int64_t w = 0;
+      if (lane < len) {
+        row_entry(s, v, lane, col, w);
+        bytes += entry_bytes(s, lane < v.a_len);
+        if (s.drop_self && col == (int32_t)r) col = -1;
+      }
+      const bool has = col >= 0;
+      const unsigned hm = __ballot_sync(0xffffffffu, has);
+      const unsigned peers = __match_any_sync(0xffffffffu, col) & hm;  // lanes with this lane's column
+      const bool lead = has && (peers & lt) == 0;                      // the lowest of them
+      unsigned long long sum = 0;
+      for (unsigned q = peers; q; q &= q - 1) {  // the column's weights, summed in every peer lane
+        const int sl = __ffs(q) - 1;
+        sum += (unsigned long long)__shfl_sync(peers, (long long)w, sl);
+      }
+      const unsigned leads = __ballot_sync(0xffffffffu, lead);
+      const int64_t ob = out_start[r];
+      if (lead) {
+        const int pos = __popc(leads & lt);
+        adj_out[ob + pos] = col;
+        W_out[ob + pos] = (int64_t)sum;
+      }
+      if (lane == 0) {
+        const int out = __popc(leads);
+        deg_out[r] = out;
+        bytes += 12ull * (unsigned long long)out + 24ull;
+      }
+    }
+  }
+  account(fam, bytes, sacc);
+}
+
 // Block per row: one hash table over the block's dynamic shared memory (TMAX entries), rows of up to
 // TMAX / 2 raw entries, taken from `list`; output positions come from a block counter (any order).
 template <int TMAX>
@@ -591,9 +670,10 @@ void merge_rows(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* 
   dfree(cnts, s);
 }
 
-// Contraction merge: rows in no particular order.  Tiers by raw length: a warp and a 256-entry table
-// (<= 128), a block of 256 threads and a 2,048-entry table (<= 1,024), a block of 1,024 threads and a
-// 16,384-entry table (<= 8,192), then the radix tier.
+// Unordered merge (symmetrisation, contraction): rows in no particular order.  Tiers by raw length: a
+// warp with the entries in registers (<= 32; only when the rows average at most 20 raw entries), a warp
+// and a 256-entry table (<= 128), a block of 256 threads and a 2,048-entry table (<= 1,024), a block of
+// 1,024 threads and a 16,384-entry table (<= 8,192), then the radix tier.
 constexpr int kHashTB2 = 2048, kHashTB3 = 16384;
 constexpr size_t kHashSmemB2 = (size_t)kHashTB2 * 12, kHashSmemB3 = (size_t)kHashTB3 * 12;
 void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const int64_t* out_start,
@@ -606,17 +686,33 @@ void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const
                                  (int)kHashSmemB3));
     attr_set = true;
   }
-  unsigned* cnts = dnew<unsigned>(4, s);  // tier-2 list, tier-3 list, huge list, unused
+  unsigned* cnts = dnew<unsigned>(4, s);  // tier-2 list, tier-3 list, huge list, tier-1 list
   GP_CUDA(cudaMemsetAsync(cnts, 0, 4 * sizeof(unsigned), s));
+  int32_t* l1 = dnew<int32_t>(nrows, s);
   int32_t* l2 = dnew<int32_t>(nrows, s);
   int32_t* l3 = dnew<int32_t>(nrows, s);
   int32_t* lh = dnew<int32_t>(nrows, s);
   const int sms = num_sms();
-  const int64_t want = (nrows + kHashW1 - 1) / kHashW1;
-  const unsigned grid1 = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
-  GP_LAUNCH(family, (k_merge_hash<kHashT1, kHashW1>), grid1, kHashW1 * 32, kHashSmem1, s, src, nrows,
-            (const int32_t*)nullptr, (const unsigned*)nullptr, out_start, deg_out, adj_out, W_out, l2, cnts,
-            (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
+  if (raw_bound <= 20 * nrows) {
+    // short rows on average (the symmetrisation: out-row + in-row): tier 0 merges rows of <= 32 raw
+    // entries in registers (a warp each, 32 rows measured per warp step) and lists the others by tier;
+    // tier 1 (a warp and a 256-entry table per row) takes its list
+    const int64_t want0 = (nrows + 255) / 256;
+    const unsigned grid0 = (unsigned)(want0 < (int64_t)sms * 16 ? want0 : (int64_t)sms * 16);
+    GP_LAUNCH(family, k_merge_match, grid0, 256, 0, s, src, nrows, out_start, deg_out, adj_out, W_out, l1,
+              cnts + 3, (int64_t)kHashT1 / 2, l2, cnts, (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh,
+              cnts + 2, family);
+    GP_LAUNCH(family, (k_merge_hash<kHashT1, kHashW1>), (unsigned)(sms * 16), kHashW1 * 32, kHashSmem1, s, src,
+              nrows, (const int32_t*)l1, (const unsigned*)(cnts + 3), out_start, deg_out, adj_out, W_out, l2, cnts,
+              (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
+  } else {
+    // longer rows (the contraction): tier 1 over every row, longer ones to their tier's list
+    const int64_t want = (nrows + kHashW1 - 1) / kHashW1;
+    const unsigned grid1 = (unsigned)(want < (int64_t)sms * 16 ? want : (int64_t)sms * 16);
+    GP_LAUNCH(family, (k_merge_hash<kHashT1, kHashW1>), grid1, kHashW1 * 32, kHashSmem1, s, src, nrows,
+              (const int32_t*)nullptr, (const unsigned*)nullptr, out_start, deg_out, adj_out, W_out, l2, cnts,
+              (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
+  }
   GP_LAUNCH(family, k_merge_hash_blk<kHashTB2>, (unsigned)(8 * sms), 256, kHashSmemB2, s, src, (const int32_t*)l2,
             (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, family);
   GP_LAUNCH(family, k_merge_hash_blk<kHashTB3>, (unsigned)sms, 1024, kHashSmemB3, s, src, (const int32_t*)l3,
@@ -630,6 +726,7 @@ void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const
   GP_CHECK_LAUNCH();
   dfree(tk, s);
   dfree(tv, s);
+  dfree(l1, s);
   dfree(l2, s);
   dfree(l3, s);
   dfree(lh, s);
