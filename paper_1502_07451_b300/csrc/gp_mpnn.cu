@@ -161,6 +161,10 @@ static void model_init_host(uint64_t seed, std::vector<float>& P) {
 // in a fixed order (the transpose fills rows in no particular order).
 static void mp_prepare(const gp_graph* gc, cudaStream_t s) {
   gp_graph* g = const_cast<gp_graph*>(gc);
+  // the sort below permutes the in-rows in place, and a deferred creation's level-ordered in-CSR build
+  // (on the side stream) reads them: wait for it first
+  const gp_status ls = levels_ready(g);
+  if (ls != GP_OK) throw Fail{ls};
   if (g->in_sorted || g->n == 0 || g->m == 0) {
     g->in_sorted = true;
     return;

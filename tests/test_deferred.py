@@ -110,3 +110,27 @@ def test_deferred_handles_in_batch_and_network_paths():
     finally:
         for x in imm + dfr:
             x.close()
+
+
+def test_deferred_network_right_after_creation():
+    """The network sorts the in-rows in place; on a deferred handle it must first wait for the level
+    work that reads them: logits and the learned split equal those of a synchronous handle."""
+    g = gen.layered(200, 1000, 1_600_000, 11)
+    model = gp.gp_model_create(5)
+    try:
+        outs = []
+        for deferred in (False, True):
+            with gp.Graph(dgraph(g), deferred=deferred) as G:
+                logits = torch.empty(g["n"], dtype=torch.float32, device="cuda")
+                gp.gp_model_forward(model, G.h, logits)
+                part = torch.empty(g["n"], dtype=torch.uint8, device="cuda")
+                res = gp.gp_partition_learned(G.h, model, part)
+                fin = torch.empty(g["n"], dtype=torch.int64, device="cuda")
+                ms = gp.gp_makespan(G.h, part, fin)
+                outs.append((logits.cpu(), part.cpu().numpy(), {k: v for k, v in res.items() if k != "ms"}, ms,
+                             fin.cpu().numpy()))
+        a, b = outs
+        assert torch.equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2] and a[3] == b[3]
+        assert np.array_equal(a[4], b[4])
+    finally:
+        gp.gp_model_destroy(model)
