@@ -239,6 +239,22 @@ def run_reference_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values (the slowest rank's time); x itself on one rank."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, timed on a bounded sample of the workload (first 100 layers)."""
     from paper_1502_07451_b300 import gen
@@ -385,12 +401,10 @@ def main():
     torch.cuda.synchronize()
     launches = gp.gp_launch_count() - launches0
     clocks = sampler.stop() if sampler else None
+    total_ms = max_over_ranks(total_ms, world)
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
-    value = world * K * m / (total_ms / 1e3)
+    value = job_rate(K * m, world, total_ms / 1e3)
 
     # ---- end to end through the C-ABI with pinned host buffers (H2D and D2H inside the timed region)
     hg = {k: torch.from_numpy(g[k]).pin_memory() for k in keys}
@@ -415,11 +429,8 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * K * m / e2e_s
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e_value = job_rate(K * m, world, e2e_s)
     e2e_ok = bool(np.array_equal(hpart.numpy(), part.cpu().numpy()))
 
     # ---- roofline: a second pass of the same K steps with CUDA events around every launch
