@@ -390,12 +390,52 @@ static void graph_free(gp_graph* g) {
 // distributed-shared-memory ring variant when two adjacent levels fit its ring, else (or when
 // GP_MAKESPAN_KERNEL=cluster) the variant that reads every predecessor from global memory.
 static cudaError_t launch_makespan(const gp_graph* g, const uint8_t* part, unsigned long long* fp,
-                                   unsigned long long* ms, int* bad, int64_t* fin, cudaStream_t s) {
+                                   unsigned long long* ms, int* bad, int64_t* fin, cudaStream_t s,
+                                   unsigned* grid_bar = nullptr) {
   const int G = makespan_group(g->n, g->m);
   const int32_t nlev = g->nlev;
   const char* forced = getenv("GP_MAKESPAN_KERNEL");
-  const bool dsm = g->max_width <= kMsR && g->m < ((int64_t)1 << 31) && g->n < ((int64_t)1 << 31) &&
-                   !(forced && strcmp(forced, "cluster") == 0);
+  const bool small_ids = g->m < ((int64_t)1 << 31) && g->n < ((int64_t)1 << 31);
+  const bool dsm = g->max_width <= kMsR && small_ids && !(forced && strcmp(forced, "cluster") == 0);
+  // levels wider than a cluster's groups: one cooperative grid (grid_bar: a zeroed counter)
+  const bool grid = !dsm && small_ids && grid_bar && (int64_t)g->max_width * G > 16 * 1024 &&
+                    !(forced && strcmp(forced, "cluster") == 0);
+  if (grid) {
+    int coop = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (coop) {
+      switch (G) {
+#define GP_MSG(GG)                                                                                     \
+  case GG: {                                                                                           \
+    int per_sm = 0;                                                                                    \
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_makespan_grid<GG>, 1024, 0) != cudaSuccess || \
+        per_sm < 1)                                                                                    \
+      break;                                                                                           \
+    const int64_t want = ((int64_t)g->max_width * GG + 1023) / 1024;                                   \
+    const int64_t cap = (int64_t)num_sms() * per_sm;                                                   \
+    const unsigned blocks = (unsigned)(want < cap ? want : cap);                                       \
+    const int64_t* a0 = (const int64_t*)g->lev_ptr;                                                    \
+    const int32_t* a1 = (const int32_t*)g->lev_vtx;                                                    \
+    const int64_t* a2 = (const int64_t*)g->lo_off;                                                     \
+    const int32_t* a3 = (const int32_t*)g->lo_src;                                                     \
+    const int32_t* a4 = (const int32_t*)g->lo_w;                                                       \
+    const int32_t* a5 = (const int32_t*)g->lo_cC;                                                      \
+    const int32_t* a6 = (const int32_t*)g->lo_cG;                                                      \
+    int32_t nl = nlev;                                                                                 \
+    void* args[] = {&nl, (void*)&a0, (void*)&a1, (void*)&a2, (void*)&a3, (void*)&a4, (void*)&a5, (void*)&a6, \
+                    (void*)&part, (void*)&fp, (void*)&ms, (void*)&bad, (void*)&fin, (void*)&grid_bar};    \
+    launch_begin(F_MAKESPAN, s);                                                                       \
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_makespan_grid<GG>, dim3(blocks),  \
+                                                      dim3(1024), args, 0, s);                         \
+    launch_end(F_MAKESPAN, s);                                                                         \
+    return e;                                                                                          \
+  }
+        GP_MSG(2) GP_MSG(4) GP_MSG(8) GP_MSG(16) GP_MSG(32)
+#undef GP_MSG
+      }
+    }
+  }
   switch (G) {
 #define GP_MS(GG)                                                                                      \
   case GG: {                                                                                           \
@@ -1072,11 +1112,11 @@ gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* makespan,
     struct Small {
       unsigned long long ms;
       int bad;
-      int pad;
+      unsigned grid_bar;  // the grid kernel's barrier counter
     };
     Small* sm = A.get<Small>(1);
     GP_CUDA(cudaMemsetAsync(sm, 0, sizeof(Small), s));
-    GP_CUDA(launch_makespan(g, p, fp, &sm->ms, &sm->bad, fin, s));
+    GP_CUDA(launch_makespan(g, p, fp, &sm->ms, &sm->bad, fin, s, &sm->grid_bar));
     Small h;
     GP_CUDA(cudaMemcpyAsync(&h, sm, sizeof(Small), cudaMemcpyDeviceToHost, s));
     if (fin_host) GP_CUDA(cudaMemcpyAsync(finish_out, fin, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, s));

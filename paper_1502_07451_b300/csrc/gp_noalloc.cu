@@ -71,7 +71,8 @@ extern "C" gp_status gp_makespan_noalloc(const gp_graph* g, const uint8_t* part,
     cudaGetLastError();
     return GP_ERR_CUDA;
   }
-  if (launch_makespan(g, part, fp, msp, badp, finish_out, s) != cudaSuccess) {
+  unsigned* grid_bar = (unsigned*)(base + 2);       // word 2: the grid kernel's barrier counter
+  if (launch_makespan(g, part, fp, msp, badp, finish_out, s, grid_bar) != cudaSuccess) {
     cudaGetLastError();
     return GP_ERR_CUDA;
   }

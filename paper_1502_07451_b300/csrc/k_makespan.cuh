@@ -423,3 +423,148 @@ __global__ void __launch_bounds__(1024)
 }
 
 }  // namespace gp
+
+namespace gp {
+
+// ------------------------------------------------------------------------------------------------
+// The same recurrence for DAGs whose levels are wider than the ring: one cooperative grid of up to one
+// CTA per SM, so that a lane group has about one vertex per level, with the two-stage lookahead of
+// k_makespan_dsm and predecessors read from the global copy (L2).  Levels are separated by a grid
+// barrier of this kernel's own: every CTA's thread 0, after its CTA's stores and a fence, adds one to
+// bar[0]; it then waits until bar[0] reaches (level + 1) x CTAs and fences again.  The waits are bounded
+// by the global timer (0.5 s): on expiry the thread sets bit 1 of *bad_part, and its CTA (deciding
+// together through __syncthreads_or) stops; the other CTAs' waits then expire too.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_wait_bounded(const unsigned* bar, unsigned target) {
+  unsigned long long t0 = 0;
+  for (uint32_t k = 0;; k++) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+    if (v >= target) return true;
+    if ((k & 63u) == 0) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (k == 0) t0 = t;
+      else if (t - t0 > 500000000ull) return false;
+    }
+  }
+}
+
+template <int G>
+__global__ void __launch_bounds__(1024, 1)
+    k_makespan_grid(int32_t nlev, const int64_t* __restrict__ lev_ptr, const int32_t* __restrict__ lev_vtx,
+                    const int64_t* __restrict__ lo_off, const int32_t* __restrict__ lo_src,
+                    const int32_t* __restrict__ lo_w, const int32_t* __restrict__ lo_cC,
+                    const int32_t* __restrict__ lo_cG, const uint8_t* __restrict__ part,
+                    unsigned long long* fp, unsigned long long* ms_out, int* bad_part,
+                    int64_t* __restrict__ finish_out, unsigned* bar) {
+  __shared__ unsigned long long sh[32];
+  __shared__ unsigned long long sacc[32];
+  const int32_t tid = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  const int32_t group = tid / G, ngroups = (int32_t)(gridDim.x * blockDim.x) / G;
+  const int sub = threadIdx.x % G;
+  const unsigned gmask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
+  unsigned long long local_max = 0, bytes = 0;
+  auto value_of = [&](const MsB& b) -> unsigned long long {
+    const uint8_t p = b.p;
+    unsigned long long best = 0;
+    const int32_t e = b.eb + sub;
+    if (b.src >= 0) {
+      const unsigned long long f = __ldcg(fp + b.src);
+      best = (f >> 1) + (((uint8_t)(f & 1ull) != p) ? (unsigned long long)b.w : 0ull);
+    }
+    if (b.src2 >= 0) {
+      const unsigned long long f = __ldcg(fp + b.src2);
+      const unsigned long long t = (f >> 1) + (((uint8_t)(f & 1ull) != p) ? (unsigned long long)b.w2 : 0ull);
+      best = t > best ? t : best;
+    }
+    for (int32_t x = e + 2 * G; x < b.ee; x += G) {
+      const unsigned long long f = __ldcg(fp + lo_src[x]);
+      const unsigned long long t = (f >> 1) + (((uint8_t)(f & 1ull) != p) ? (unsigned long long)lo_w[x] : 0ull);
+      best = t > best ? t : best;
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const unsigned long long q = __shfl_xor_sync(gmask, best, o, G);
+      best = q > best ? q : best;
+    }
+    const unsigned long long fin = best + (unsigned long long)(p ? b.cG : b.cC);
+    if (sub == 0) {
+      if (p > 1) atomicOr(bad_part, 1);
+      local_max = fin > local_max ? fin : local_max;
+      bytes += 4ull + 1ull + 16ull + (unsigned long long)(b.ee - b.eb) * 16ull + 4ull + 8ull;
+    }
+    return (fin << 1) | (unsigned long long)(p & 1);
+  };
+  auto lp = [&](int32_t l) -> int32_t { return (int32_t)lev_ptr[l < nlev ? l : nlev]; };
+  int32_t beg = lp(0), end = lp(1), end1 = lp(2), end2 = lp(3), end3 = lp(4);
+  MsA a1, a2;
+  MsB cur, b1;
+  {
+    MsA a0;
+    ms_load_a(a0, beg + group, end, lev_vtx, lo_off, lo_cC, lo_cG);
+    ms_load_a(a1, end + group, end1, lev_vtx, lo_off, lo_cC, lo_cG);
+    ms_load_b<G>(cur, a0, sub, lo_src, lo_w, part);
+  }
+  bool failed = false;
+  for (int32_t l = 0; l < nlev; l++) {
+    if (__syncthreads_or(failed)) break;  // a wait gave up: this CTA stops (the others' waits expire)
+    if (cur.valid) {
+      const unsigned long long pk = value_of(cur);
+      if (sub == 0) {
+        fp[cur.i] = pk;
+        if (finish_out) finish_out[lev_vtx[cur.i]] = (int64_t)(pk >> 1);
+      }
+    }
+    for (int32_t i = beg + group + ngroups; i < end; i += ngroups) {  // levels wider than the groups
+      MsA a;
+      MsB b;
+      ms_load_a(a, i, end, lev_vtx, lo_off, lo_cC, lo_cG);
+      ms_load_b<G>(b, a, sub, lo_src, lo_w, part);
+      const unsigned long long pk = value_of(b);
+      if (sub == 0) {
+        fp[i] = pk;
+        if (finish_out) finish_out[a.v] = (int64_t)(pk >> 1);
+      }
+    }
+    // lookahead, then the grid barrier
+    ms_load_b<G>(b1, a1, sub, lo_src, lo_w, part);
+    ms_load_a(a2, end1 + group, end2, lev_vtx, lo_off, lo_cC, lo_cG);
+    const int32_t end4 = lp(l + 5);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this CTA's finish times before its arrival
+      atomicAdd(bar, 1u);
+      if (!grid_wait_bounded(bar, (unsigned)(l + 1) * gridDim.x)) {
+        failed = true;
+        atomicOr(bad_part, 2);
+      }
+      __threadfence();
+    }
+    cur = b1;
+    a1 = a2;
+    beg = end;
+    end = end1;
+    end1 = end2;
+    end2 = end3;
+    end3 = end4;
+  }
+  {
+    unsigned long long x = local_max;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long q = __shfl_xor_sync(0xffffffffu, x, o);
+      x = q > x ? q : x;
+    }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long mx = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) mx = sh[w] > mx ? sh[w] : mx;
+      if (mx) atomicMax(ms_out, mx);
+    }
+  }
+  account(F_MAKESPAN, bytes, sacc);
+}
+
+}  // namespace gp

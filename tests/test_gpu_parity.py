@@ -335,12 +335,14 @@ def _long_range_chain(n, stride, seed):
 
 
 def test_makespan_kernels_agree_with_oracle():
-    """Both makespan kernels (by default the cluster kernel with a distributed-shared-memory ring of
-    recent finish times, exchanged by st.async, where every level fits it; GP_MAKESPAN_KERNEL=cluster: every
-    predecessor from global memory) on graphs that reach each branch: levels narrow enough for the
-    ring, levels too wide for it, predecessors beyond the ring, one-vertex levels, several lanes per
-    vertex, levels wider than the cluster's groups."""
+    """Every makespan kernel against the oracle (by default: the cluster kernel with a distributed-
+    shared-memory ring of recent finish times, exchanged by st.async, where every level fits it; a
+    cooperative grid with its own bounded grid barrier where levels are wider than a cluster's groups;
+    GP_MAKESPAN_KERNEL=cluster: one cluster reading every predecessor from global memory) on graphs that
+    reach each branch: levels narrow enough for the ring, levels too wide for it, predecessors beyond
+    the ring, one-vertex levels, several lanes per vertex, levels wider than the groups."""
     graphs = [gen.layered(30, 1000, 240000, 1), gen.layered(12, 3000, 300000, 2), gen.layered(6, 5000, 200000, 9),
+              gen.layered(5, 12000, 400000, 12),  # wider than the ring and a cluster's groups: the grid kernel
               gen.layered(4, 1500, 60000, 3), gen.random_dag(3000, 12000, 4), gen.random_dag(300, 12000, 6),
               _long_range_chain(30000, 97, 5), FIXTURES["hub1000"](), gen.cholesky(16)]
     old = os.environ.get("GP_MAKESPAN_KERNEL")
