@@ -188,14 +188,14 @@ __device__ void b_pick_round(const LevelGraph& g, long long capC, long long capG
   if (picked) *s_flag = 1;
 }
 template <int G>
-__device__ void b_anchor(const LevelGraph& g, uint64_t seed, const int32_t* mate, int32_t* anchor,
-                         uint8_t* is_anchor) {
-  match_anchor<G>(g, seed, mate, anchor, is_anchor, threadIdx.x, blockDim.x);
+__device__ void b_anchor(const LevelGraph& g, uint64_t seed, const int32_t* mate, int32_t* anchor, int32_t* scnt) {
+  match_anchor<G>(g, seed, mate, anchor, nullptr, threadIdx.x, blockDim.x, scnt);
 }
 
 __device__ void b_match(const LevelGraph& g, long long capC, long long capG, uint64_t seed, int G, int32_t* mate,
                         int32_t* pick, uint8_t* alive, int32_t* biglist, int32_t* sat, uint32_t* bits,
-                        unsigned char* dsm, int* s_flag, unsigned* s_cnt, long long* s_red) {
+                        unsigned char* dsm, int* s_flag, unsigned* s_cnt, long long* s_red, int32_t* scnt,
+                        int32_t* soff, int32_t* bucket) {
   const int64_t n = g.n;
   long long mC = 0, mG = 0;
   for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
@@ -237,19 +237,40 @@ __device__ void b_match(const LevelGraph& g, long long capC, long long capG, uin
     if (*s_flag == 0) break;  // no new pair: the next round would see the same state
     __syncthreads();
   }
-  // two-hop pairing
+  // two-hop pairing, from anchor buckets: each unmatched vertex counts itself into its anchor's bucket,
+  // a scan gives the buckets' offsets, the vertices are scattered into them, and a warp per anchor
+  // pairs its bucket (scnt / soff / bucket: n, n + 1 and n entries of scratch)
   int32_t* anchor = pick;
-  uint8_t* is_anchor = alive;
-  for (int64_t v = threadIdx.x; v < n; v += blockDim.x) is_anchor[v] = 0;
+  for (int64_t v = threadIdx.x; v < n; v += blockDim.x) scnt[v] = 0;
   __syncthreads();
   switch (G) {
-    case 2: b_anchor<2>(g, seed, mate, anchor, is_anchor); break;
-    case 4: b_anchor<4>(g, seed, mate, anchor, is_anchor); break;
-    case 8: b_anchor<8>(g, seed, mate, anchor, is_anchor); break;
-    case 16: b_anchor<16>(g, seed, mate, anchor, is_anchor); break;
-    default: b_anchor<32>(g, seed, mate, anchor, is_anchor); break;
+    case 2: b_anchor<2>(g, seed, mate, anchor, scnt); break;
+    case 4: b_anchor<4>(g, seed, mate, anchor, scnt); break;
+    case 8: b_anchor<8>(g, seed, mate, anchor, scnt); break;
+    case 16: b_anchor<16>(g, seed, mate, anchor, scnt); break;
+    default: b_anchor<32>(g, seed, mate, anchor, scnt); break;
   }
-  if (threadIdx.x == 0) *s_cnt = 0;
+  __syncthreads();
+  {
+    long long run = 0;
+    for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
+      const int64_t v = b0 + threadIdx.x;
+      const long long x = v < n ? scnt[v] : 0;
+      long long tot;
+      const long long inc = cta_scan_incl<long long>(x, s_red, tot);
+      if (v < n) soff[v] = (int32_t)(run + inc - x);
+      run += tot;
+    }
+    if (threadIdx.x == 0) {
+      soff[n] = (int32_t)run;
+      *s_cnt = 0;
+    }
+  }
+  __syncthreads();
+  for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+    const int32_t a = anchor[v];
+    if (a >= 0) bucket[soff[a] + atomicSub(&scnt[a], 1) - 1] = (int32_t)v;
+  }
   __syncthreads();
   const int nbits = bits_for(n);
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -258,8 +279,8 @@ __device__ void b_match(const LevelGraph& g, long long capC, long long capG, uin
     int32_t* S0 = (int32_t*)(dsm + (size_t)wib * kBatchWarpSmem);
     int32_t* S1 = S0 + 256;
     int* hist = (int*)(S0 + 512);
-    twohop_warps(g, capC, capG, anchor, is_anchor, mate, biglist, s_cnt, nbits, wib, blockDim.x >> 5, S0, S1, hist,
-                 256, bytes);
+    twohop_bucket_warps<int32_t>(g, capC, capG, soff, bucket, mate, biglist, s_cnt, nbits, wib, blockDim.x >> 5, S0,
+                                 S1, hist, 256, bytes);
   }
   __syncthreads();
   const unsigned nbig = *s_cnt;
@@ -269,13 +290,13 @@ __device__ void b_match(const LevelGraph& g, long long capC, long long capG, uin
     const int32_t h = biglist[bi];
     for (int64_t q = threadIdx.x; q < nwords; q += blockDim.x) bits[q] = 0u;
     __syncthreads();
-    const int64_t b = g.start[h];
-    const int32_t d = g.deg[h];
-    for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {
-      const int32_t v = g.adj[b + q];
-      if (anchor[v] == h) atomicOr(&bits[v >> 5], 1u << (v & 31));
+    const int32_t b = soff[h];
+    const int32_t d = soff[h + 1] - b;
+    for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {  // the bucket's vertices, as a bitmap
+      const int32_t v = bucket[b + q];
+      atomicOr(&bits[v >> 5], 1u << (v & 31));
     }
-    bytes += 8ull * (unsigned long long)((d + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x);
+    bytes += 4ull * (unsigned long long)((d + (int)blockDim.x - 1 - (int)threadIdx.x) / (int)blockDim.x);
     __syncthreads();
     if (wib == 0) {
       int64_t k = 0;
@@ -726,7 +747,9 @@ __device__ void batch_graph(const BatchGraph& B, BatchOut* out, char* slot, unsi
     if (!(f.n > kCoarsest && L < kMaxLevels)) break;
     const LevelGraph g = lev_view(f);
     const int G = lanes_for_degree(f.a, f.n, sch.gshift);
-    b_match(g, capC, capG, B.seed, G, mate, pick, alive, biglist, sat, bits, dsm, &s_flag, &s_cnt, s_red);
+    // scratch of the two-hop buckets: arrays the refinement uses later (idle while coarsening)
+    b_match(g, capC, capG, B.seed, G, mate, pick, alive, biglist, sat, bits, dsm, &s_flag, &s_cnt, s_red,
+            cand.dirty[0], (int32_t*)cand.cd, cand.dirty[1]);
     __syncthreads();
     long long reps = 0;
     for (int64_t v = threadIdx.x; v < f.n; v += blockDim.x) {

@@ -397,80 +397,19 @@ __device__ int32_t* warp_radix_keys(int32_t* A, int32_t* B, int k, int nbits, in
   return A;
 }
 
-// Warp per anchor: gathers its anchored vertices (rows are in no particular order), sorts them and
-// pairs them.  Anchors with more than `cap` of them go to the list `big`.  `gw` / `nw`: this warp
-// and the number of warps sharing the level; S0 / S1 (cap keys each) and hist (256) are the warp's
-// shared-memory buffers.
-__device__ void twohop_warps(const LevelGraph& g, int64_t capC, int64_t capG, const int32_t* __restrict__ anchor,
-                             const uint8_t* __restrict__ is_anchor, int32_t* __restrict__ mate,
-                             int32_t* __restrict__ big, unsigned* big_cnt, int nbits, int64_t gw, int64_t nw,
-                             int32_t* S0, int32_t* S1, int* hist, int cap, unsigned long long& bytes) {
+// Warp per anchor, from the anchors' buckets (sat[soff[h] .. soff[h + 1])): loads its bucket, sorts it and
+// pairs it in ascending vertex order (pair_sorted).
+// Buckets of more than `cap` go to the list `big`.  `gw` / `nw`: this warp and the number of warps
+// sharing the level; S0 / S1 (cap keys each) and hist (256) are the warp's shared-memory buffers.
+template <class Off>
+__device__ void twohop_bucket_warps(const LevelGraph& g, int64_t capC, int64_t capG, const Off* __restrict__ soff,
+                                    const int32_t* __restrict__ sat, int32_t* __restrict__ mate,
+                                    int32_t* __restrict__ big, unsigned* big_cnt, int nbits, int64_t gw, int64_t nw,
+                                    int32_t* S0, int32_t* S1, int* hist, int cap, unsigned long long& bytes) {
   const int lane = threadIdx.x & 31;
-  const unsigned lt = lanemask_lt();
-  int32_t* S = S0;
-  for (int64_t hb = gw * 32; hb < g.n; hb += nw * 32) {
-    unsigned am = __ballot_sync(0xffffffffu, hb + lane < g.n && is_anchor[hb + lane]);
-    while (am) {
-      const int64_t h = hb + __ffs(am) - 1;
-      am &= am - 1;
-      const int64_t b = g.start[h];
-      const int32_t d = g.deg[h];
-      int k = 0;
-      bool over = false;
-      for (int32_t base = 0; base < d; base += 32) {
-        const int32_t q = base + lane;
-        int32_t v = -1;
-        bool flag = false;
-        if (q < d) {
-          v = g.adj[b + q];
-          flag = anchor[v] == (int32_t)h;
-          bytes += 8;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, flag);
-        if (k + __popc(m) > cap) {
-          over = true;
-          break;
-        }
-        if (flag) S[k + __popc(m & lt)] = v;
-        k += __popc(m);
-      }
-      if (over) {
-        if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
-        continue;
-      }
-      if (k == 0) continue;
-      __syncwarp();
-      const int32_t* sorted = S;
-      if (k <= 32) {
-        const int32_t x = warp_sort32(lane < k ? S[lane] : INT32_MAX, lane);
-        __syncwarp();
-        S[lane] = x;
-        __syncwarp();
-      } else {
-        sorted = warp_radix_keys(S, S1, k, nbits, hist);
-      }
-      pair_sorted(g, capC, capG, sorted, k, mate, bytes);
-      __syncwarp();
-    }
-  }
-}
-// Warp per anchor, from the anchors' buckets: loads its bucket, sorts it and pairs it (the pairing of
-// twohop_warps, which finds the same vertices by scanning the anchor's row).  Buckets of more than
-// kSatCap go to the list `big`.
-__global__ void __launch_bounds__(kTwohopWarps * 32)
-    k_twohop_b(LevelGraph g, int64_t capC, int64_t capG, const int64_t* __restrict__ soff,
-               const int32_t* __restrict__ sat, int32_t* __restrict__ mate, int32_t* __restrict__ big,
-               unsigned* big_cnt, int nbits) {
-  __shared__ int32_t sbuf[kTwohopWarps][2][kSatCap];
-  __shared__ int hist_all[kTwohopWarps][256];
-  __shared__ unsigned long long sacc[32];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gw = (int64_t)blockIdx.x * kTwohopWarps + wib, nw = (int64_t)gridDim.x * kTwohopWarps;
-  int32_t* S = sbuf[wib][0];
-  unsigned long long bytes = 0;
   for (int64_t hb = gw * 32; hb < g.n; hb += nw * 32) {
     const int64_t h0 = hb + lane;
-    const int64_t lo = h0 < g.n ? soff[h0] : 0, hi = h0 < g.n ? soff[h0 + 1] : 0;
+    const int64_t lo = h0 < g.n ? (int64_t)soff[h0] : 0, hi = h0 < g.n ? (int64_t)soff[h0 + 1] : 0;
     unsigned am = __ballot_sync(0xffffffffu, hi > lo);
     while (am) {
       const int src = __ffs(am) - 1;
@@ -478,26 +417,40 @@ __global__ void __launch_bounds__(kTwohopWarps * 32)
       const int64_t h = hb + src;
       const int64_t b = __shfl_sync(0xffffffffu, lo, src);
       const int k = (int)(__shfl_sync(0xffffffffu, hi, src) - b);
-      if (k > kSatCap) {
+      if (k > cap) {
         if (lane == 0) big[atomicAdd(big_cnt, 1u)] = (int32_t)h;
         continue;
       }
-      for (int q = lane; q < k; q += 32) S[q] = sat[b + q];
+      for (int q = lane; q < k; q += 32) S0[q] = sat[b + q];
       bytes += 4ull * (unsigned long long)k;
       __syncwarp();
-      const int32_t* sorted = S;
+      const int32_t* sorted = S0;
       if (k <= 32) {
-        const int32_t x = warp_sort32(lane < k ? S[lane] : INT32_MAX, lane);
+        const int32_t x = warp_sort32(lane < k ? S0[lane] : INT32_MAX, lane);
         __syncwarp();
-        S[lane] = x;
+        S0[lane] = x;
         __syncwarp();
       } else {
-        sorted = warp_radix_keys(S, sbuf[wib][1], k, nbits, hist_all[wib]);
+        sorted = warp_radix_keys(S0, S1, k, nbits, hist);
       }
       pair_sorted(g, capC, capG, sorted, k, mate, bytes);
       __syncwarp();
     }
   }
+}
+
+__global__ void __launch_bounds__(kTwohopWarps * 32)
+    k_twohop_b(LevelGraph g, int64_t capC, int64_t capG, const int64_t* __restrict__ soff,
+               const int32_t* __restrict__ sat, int32_t* __restrict__ mate, int32_t* __restrict__ big,
+               unsigned* big_cnt, int nbits) {
+  __shared__ int32_t sbuf[kTwohopWarps][2][kSatCap];
+  __shared__ int hist_all[kTwohopWarps][256];
+  __shared__ unsigned long long sacc[32];
+  const int wib = threadIdx.x >> 5;
+  unsigned long long bytes = 0;
+  twohop_bucket_warps<int64_t>(g, capC, capG, soff, sat, mate, big, big_cnt, nbits,
+                               (int64_t)blockIdx.x * kTwohopWarps + wib, (int64_t)gridDim.x * kTwohopWarps,
+                               sbuf[wib][0], sbuf[wib][1], hist_all[wib], kSatCap, bytes);
   account(F_TWOHOP, bytes, sacc);
 }
 
