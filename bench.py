@@ -239,6 +239,14 @@ def run_reference_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def quiet_heap():
+    """Collect the heap once and freeze it, so that no garbage-collection pass over the (large) input
+    graphs lands in a timed region."""
+    import gc
+    gc.collect()
+    gc.freeze()
+
+
 def max_over_ranks(x, world, device="cuda"):
     """The largest of the ranks' values (the slowest rank's time); x itself on one rank."""
     if world == 1:
@@ -380,11 +388,7 @@ def main():
     torch.cuda.synchronize()
     if bgen is not None:
         bgen.wait()
-    # the batch graphs and the held-out graphs make a large heap: collect it once and freeze it, so that
-    # no garbage-collection pass over it lands in a timed region
-    import gc
-    gc.collect()
-    gc.freeze()
+    quiet_heap()  # the batch graphs and the held-out graphs make a large heap
 
     # ---- timed device pass
     sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
@@ -780,6 +784,7 @@ def run_batch_line(args, rank, world, local_rank, bgen):
     graphs = bgen.graphs()
     bgen.wait()
     bgen.close()
+    quiet_heap()
     sampler = ClockSampler(physical_index(local_rank)) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -873,6 +878,7 @@ def run_cholesky_line(args, rank, world, local_rank):
         for _ in range(W):
             r = fn()
         torch.cuda.synchronize()
+        quiet_heap()
         tot = 0.0
         for _ in range(K):
             flush.fill_(1)
