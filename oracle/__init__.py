@@ -109,6 +109,8 @@ def lib():
             L.og_refine.argtypes = [_I64, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]
             L.og_partition.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, C.c_double, C.c_double,
                                        C.c_uint64, _P, _P, _P]
+            L.og_partition_fixed.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
+                                             C.c_uint64, _P, _P, _P]
             L.og_cut.argtypes = [_I64, _P, _P, _P, _P, _P]
             L.og_levels.argtypes = [_I64, _I64, _P, _P, _P, _P]
             L.og_makespan.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -263,15 +265,26 @@ def refine(n, off, adj, W, vC, vG, bound_cpu, bound_gpu, part):
     return p[:n], {f[0]: int(getattr(st, f[0])) for f in RefineStats._fields_}
 
 
-def partition(g, r_cpu: float = -1.0, tol: float = 0.03, seed: int = 0, trace: bool = False):
-    """The whole bipartitioner: (part, result dict[, trace dict])."""
+def partition(g, r_cpu: float = -1.0, tol: float = 0.03, seed: int = 0, trace: bool = False, fixed=None):
+    """The whole bipartitioner: (part, result dict[, trace dict]).  fixed: None, or int8 per vertex
+    (0 pinned to the CPU, 1 to the GPU, -1 free)."""
     off, cols, w, cc, cg = _graph_arrays(g)
     n = g["n"]
     part = np.zeros(max(n, 1), np.uint8)
     res = Result()
     tr = Trace()
-    _check(lib().og_partition(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), r_cpu, tol, seed,
-                              _p(part), C.byref(res), C.byref(tr) if trace else None), "og_partition")
+    tr_p = C.byref(tr) if trace else None
+    if fixed is None:
+        _check(lib().og_partition(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), r_cpu, tol, seed,
+                                  _p(part), C.byref(res), tr_p), "og_partition")
+    else:
+        fx = _c(fixed, np.int8)
+        if fx.shape[0] != n:
+            raise ValueError("fixed must hold one value per vertex")
+        if n == 0:
+            fx = np.zeros(1, np.int8)
+        _check(lib().og_partition_fixed(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), _p(fx), r_cpu, tol,
+                                        seed, _p(part), C.byref(res), tr_p), "og_partition_fixed")
     if trace:
         return part[:n], res.as_dict(), tr.as_dict()
     return part[:n], res.as_dict()

@@ -229,9 +229,16 @@ static int og_key_better(const og_edge_key* x, const og_edge_key* y) {
   return x->mx < y->mx;
 }
 
-int og_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
-             const int64_t* vC, const int64_t* vG, int64_t capC, int64_t capG, uint64_t seed,
-             int32_t rounds, int32_t* mate) {
+/* Fixed vertices (the paper's host-source kernel, Sec. III.B, generalised): fix[v] = 0 pins v to the
+ * CPU, 1 to the GPU, -1 leaves it free; fix == NULL means every vertex is free.  Two vertices may merge
+ * unless they are pinned to different sides; a coarse vertex is pinned where either member is. */
+static int og_compatible(const int8_t* fix, int64_t a, int64_t b) {
+  return !fix || fix[a] < 0 || fix[b] < 0 || fix[a] == fix[b];
+}
+
+static int og_match_fix(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                        const int64_t* vC, const int64_t* vG, const int8_t* fix, int64_t capC,
+                        int64_t capG, uint64_t seed, int32_t rounds, int32_t* mate) {
   int32_t* pick = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
   if (!pick) return OG_ERR_OOM;
   for (int64_t v = 0; v < n; v++) mate[v] = -1;
@@ -245,6 +252,7 @@ int og_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W
         const int32_t u = adj[e];
         if (mate[u] != -1) continue;
         if (vC[v] + vC[u] > capC || vG[v] + vG[u] > capG) continue;
+        if (!og_compatible(fix, v, u)) continue;
         og_edge_key k;
         k.W = W[e];
         k.mn = (uint32_t)(v < u ? v : u);
@@ -268,6 +276,12 @@ int og_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W
   return OG_OK;
 }
 
+int og_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+             const int64_t* vC, const int64_t* vG, int64_t capC, int64_t capG, uint64_t seed,
+             int32_t rounds, int32_t* mate) {
+  return og_match_fix(n, off, adj, W, vC, vG, NULL, capC, capG, seed, rounds, mate);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Coarsening step 1b: two-hop pairing of the vertices the handshake rounds   */
 /* left unmatched.                                                           */
@@ -282,9 +296,9 @@ int og_match(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W
 /* fit the caps, and otherwise becomes the pending one.  Paired vertices need */
 /* not be adjacent.  Anchors are all chosen before any pairing.              */
 /* ------------------------------------------------------------------------ */
-int og_match_twohop(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
-                    const int64_t* vC, const int64_t* vG, int64_t capC, int64_t capG,
-                    uint64_t seed, int32_t* mate) {
+static int og_match_twohop_fix(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                               const int64_t* vC, const int64_t* vG, const int8_t* fix, int64_t capC,
+                               int64_t capG, uint64_t seed, int32_t* mate) {
   int32_t* anchor = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
   if (!anchor) return OG_ERR_OOM;
   for (int64_t v = 0; v < n; v++) {
@@ -312,7 +326,8 @@ int og_match_twohop(int64_t n, const int64_t* off, const int32_t* adj, const int
     for (int64_t e = off[h]; e < off[h + 1]; e++) {
       const int32_t v = adj[e];
       if (anchor[v] != (int32_t)h) continue;
-      if (pending >= 0 && vC[pending] + vC[v] <= capC && vG[pending] + vG[v] <= capG) {
+      if (pending >= 0 && vC[pending] + vC[v] <= capC && vG[pending] + vG[v] <= capG &&
+          og_compatible(fix, pending, v)) {
         mate[pending] = v;
         mate[v] = pending;
         pending = -1;
@@ -323,6 +338,12 @@ int og_match_twohop(int64_t n, const int64_t* off, const int32_t* adj, const int
   }
   free(anchor);
   return OG_OK;
+}
+
+int og_match_twohop(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                    const int64_t* vC, const int64_t* vG, int64_t capC, int64_t capG,
+                    uint64_t seed, int32_t* mate) {
+  return og_match_twohop_fix(n, off, adj, W, vC, vG, NULL, capC, capG, seed, mate);
 }
 
 /* Number of coarse vertices the matching yields: one per unmatched vertex and
@@ -414,18 +435,31 @@ int og_contract(int64_t n, const int64_t* off, const int32_t* adj, const int64_t
 /* One trial: grow a CPU region from `start` (all others on the GPU).  side,
  * toC (W to the CPU region) and adjC (CPU neighbours) are caller scratch of
  * n entries; wsum[v] is v's total adjacency weight.  Returns the cut. */
+/* With fixed vertices, the CPU-pinned ones start (and stay) in the CPU region, the GPU-pinned ones on
+ * the GPU, and only free vertices move. */
 static int64_t og_grow(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
-                       const int64_t* vC, const int64_t* vG, const int64_t* wsum, int64_t BC,
-                       int64_t BG, int64_t start, uint8_t* side, int64_t* toC, int64_t* adjC,
-                       int64_t* LC_out, int64_t* LG_out) {
+                       const int64_t* vC, const int64_t* vG, const int8_t* fix, const int64_t* wsum,
+                       int64_t BC, int64_t BG, int64_t start, uint8_t* side, int64_t* toC,
+                       int64_t* adjC, int64_t* LC_out, int64_t* LG_out) {
   int64_t LC = 0, LG = 0;
   for (int64_t v = 0; v < n; v++) {
-    side[v] = 1;
+    side[v] = (fix && fix[v] == 0) ? 0 : 1;
     toC[v] = 0;
     adjC[v] = 0;
-    LG += vG[v];
   }
-  int64_t x = (vC[start] <= BC) ? start : -1;
+  for (int64_t v = 0; v < n; v++) {
+    if (side[v] == 1) {
+      LG += vG[v];
+      continue;
+    }
+    LC += vC[v];
+    for (int64_t e = off[v]; e < off[v + 1]; e++) {
+      toC[adj[e]] += W[e];
+      adjC[adj[e]] += 1;
+    }
+  }
+  const int start_free = !fix || fix[start] < 0;
+  int64_t x = (start_free && LC + vC[start] <= BC) ? start : -1;
   for (;;) {
     if (x >= 0) { /* move x to the CPU */
       side[x] = 0;
@@ -442,7 +476,7 @@ static int64_t og_grow(int64_t n, const int64_t* off, const int32_t* adj, const 
     int x_adj = 0;
     int64_t x_gain = 0;
     for (int64_t v = 0; v < n; v++) {
-      if (side[v] != 1 || LC + vC[v] > BC) continue;
+      if (side[v] != 1 || (fix && fix[v] >= 0) || LC + vC[v] > BC) continue;
       const int a = adjC[v] > 0;
       const int64_t g = 2 * toC[v] - wsum[v];
       if (x < 0 || a > x_adj || (a == x_adj && g > x_gain)) {
@@ -479,20 +513,27 @@ int og_gggp_grow(int64_t n, const int64_t* off, const int32_t* adj, const int64_
     for (int64_t e = off[v]; e < off[v + 1]; e++) wsum[v] += W[e];
   }
   int64_t LC, LG;
-  *cut_out = og_grow(n, off, adj, W, vC, vG, wsum, BC, BG, start, part, toC, adjC, &LC, &LG);
+  *cut_out = og_grow(n, off, adj, W, vC, vG, NULL, wsum, BC, BG, start, part, toC, adjC, &LC, &LG);
   free(toC);
   free(adjC);
   free(wsum);
   return OG_OK;
 }
 
-int og_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
-            const int64_t* vG, int64_t BC, int64_t BG, uint64_t seed, uint8_t* part,
-            int32_t* trial_out) {
-  int64_t SG = 0;
-  for (int64_t v = 0; v < n; v++) SG += vG[v];
-  if (SG <= BG || n == 0) {
-    for (int64_t v = 0; v < n; v++) part[v] = 1;
+/* With fixed vertices the pre-check is on the split that keeps every free vertex on the GPU (the
+ * CPU-pinned ones on the CPU); without, that split is all-GPU and its CPU load is 0. */
+static int og_gggp_fix(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                       const int64_t* vC, const int64_t* vG, const int8_t* fix, int64_t BC, int64_t BG,
+                       uint64_t seed, uint8_t* part, int32_t* trial_out) {
+  int64_t LC0 = 0, LG0 = 0;
+  for (int64_t v = 0; v < n; v++) {
+    if (fix && fix[v] == 0)
+      LC0 += vC[v];
+    else
+      LG0 += vG[v];
+  }
+  if ((LC0 <= BC && LG0 <= BG) || n == 0) {
+    for (int64_t v = 0; v < n; v++) part[v] = (fix && fix[v] == 0) ? 0 : 1;
     *trial_out = -1;
     return OG_OK;
   }
@@ -516,7 +557,7 @@ int og_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
   for (int t = 0; t < OG_TRIALS; t++) {
     const int64_t s = (int64_t)(og_hash(seed, 0xFFFFFFFFu, (uint32_t)t) % (uint64_t)n);
     int64_t LC, LG;
-    const int64_t cut = og_grow(n, off, adj, W, vC, vG, wsum, BC, BG, s, side, toC, adjC, &LC, &LG);
+    const int64_t cut = og_grow(n, off, adj, W, vC, vG, fix, wsum, BC, BG, s, side, toC, adjC, &LC, &LG);
     const int feas = (LC <= BC && LG <= BG);
     if (best_t < 0 || feas > best_feas || (feas == best_feas && cut < best_cut)) {
       best_t = t;
@@ -531,6 +572,12 @@ int og_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
   free(adjC);
   free(wsum);
   return OG_OK;
+}
+
+int og_gggp(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W, const int64_t* vC,
+            const int64_t* vG, int64_t BC, int64_t BG, uint64_t seed, uint8_t* part,
+            int32_t* trial_out) {
+  return og_gggp_fix(n, off, adj, W, vC, vG, NULL, BC, BG, seed, part, trial_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -581,9 +628,10 @@ static void og_gains(int64_t n, const int64_t* off, const int32_t* adj, const in
   }
 }
 
-int og_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
-              const int64_t* vC, const int64_t* vG, int64_t BC, int64_t BG, uint8_t* part,
-              og_refine_stats* st) {
+/* Fixed vertices are never candidates, neither of the balance round nor of a gain round. */
+static int og_refine_fix(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+                         const int64_t* vC, const int64_t* vG, const int8_t* fix, int64_t BC,
+                         int64_t BG, uint8_t* part, og_refine_stats* st) {
   int64_t* gain = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
   og_cand* cand = (og_cand*)malloc((size_t)(n > 0 ? n : 1) * sizeof(og_cand));
   if (!gain || !cand) {
@@ -613,7 +661,7 @@ int og_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* 
     og_gains(n, off, adj, W, part, gain);
     int64_t nc = 0;
     for (int64_t v = 0; v < n; v++)
-      if (part[v] == s) {
+      if (part[v] == s && !(fix && fix[v] >= 0)) {
         cand[nc].gain = gain[v];
         cand[nc].id = (int32_t)v;
         nc++;
@@ -663,7 +711,7 @@ int og_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* 
     og_gains(n, off, adj, W, part, gain);
     int64_t nc = 0;
     for (int64_t v = 0; v < n; v++)
-      if (part[v] == src && gain[v] > 0) {
+      if (part[v] == src && gain[v] > 0 && !(fix && fix[v] >= 0)) {
         cand[nc].gain = gain[v];
         cand[nc].id = (int32_t)v;
         nc++;
@@ -701,6 +749,12 @@ int og_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* 
   free(gain);
   free(cand);
   return OG_OK;
+}
+
+int og_refine(int64_t n, const int64_t* off, const int32_t* adj, const int64_t* W,
+              const int64_t* vC, const int64_t* vG, int64_t BC, int64_t BG, uint8_t* part,
+              og_refine_stats* st) {
+  return og_refine_fix(n, off, adj, W, vC, vG, NULL, BC, BG, part, st);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -743,6 +797,7 @@ typedef struct {
   int64_t n, a;
   int64_t *off, *W, *vC, *vG;
   int32_t *adj, *cmap;
+  int8_t* fix; /* NULL: no fixed vertices */
 } og_level;
 
 static void og_level_free(og_level* L) {
@@ -752,14 +807,19 @@ static void og_level_free(og_level* L) {
   free(L->vG);
   free(L->adj);
   free(L->cmap);
+  free(L->fix);
   memset(L, 0, sizeof(*L));
 }
 
-int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
-                 const int32_t* cC, const int32_t* cG, double r_cpu, double tol, uint64_t seed,
-                 uint8_t* part, og_result* res, og_trace* trace) {
+int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* cols,
+                       const int32_t* w, const int32_t* cC, const int32_t* cG, const int8_t* fixed,
+                       double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
+                       og_trace* trace) {
   int st = og_validate(n, m, off, cols, w, cC, cG);
   if (st != OG_OK) return st;
+  if (fixed)
+    for (int64_t v = 0; v < n; v++)
+      if (fixed[v] < -1 || fixed[v] > 1) return OG_ERR_INVALID;
   int64_t SC = 0, SG = 0;
   for (int64_t v = 0; v < n; v++) {
     SC += cC[v];
@@ -794,6 +854,11 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
     lv[0].vC[v] = cC[v];
     lv[0].vG[v] = cG[v];
   }
+  if (fixed) {
+    lv[0].fix = (int8_t*)malloc((size_t)n);
+    if (!lv[0].fix) goto done;
+    memcpy(lv[0].fix, fixed, (size_t)n);
+  }
   st = og_symmetrize(n, m, off, cols, w, lv[0].off, lv[0].adj, lv[0].W, &lv[0].a);
   if (st != OG_OK) {
     rc = st;
@@ -807,9 +872,10 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
     og_level* f = &lv[L];
     int32_t* mate = (int32_t*)malloc((size_t)f->n * sizeof(int32_t));
     if (!mate) goto done;
-    if (og_match(f->n, f->off, f->adj, f->W, f->vC, f->vG, capC, capG, seed, OG_MATCH_ROUNDS,
-                 mate) != OG_OK ||
-        og_match_twohop(f->n, f->off, f->adj, f->W, f->vC, f->vG, capC, capG, seed, mate) != OG_OK) {
+    if (og_match_fix(f->n, f->off, f->adj, f->W, f->vC, f->vG, f->fix, capC, capG, seed,
+                     OG_MATCH_ROUNDS, mate) != OG_OK ||
+        og_match_twohop_fix(f->n, f->off, f->adj, f->W, f->vC, f->vG, f->fix, capC, capG, seed,
+                            mate) != OG_OK) {
       free(mate);
       goto done;
     }
@@ -833,6 +899,13 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
                      c->adj, c->W, c->vC, c->vG, &c->a);
     free(mate);
     if (st != OG_OK) goto done;
+    if (f->fix) { /* a coarse vertex is pinned where a member is (members are compatible) */
+      c->fix = (int8_t*)malloc((size_t)(nc > 0 ? nc : 1));
+      if (!c->fix) goto done;
+      for (int64_t x = 0; x < nc; x++) c->fix[x] = -1;
+      for (int64_t v = 0; v < f->n; v++)
+        if (f->fix[v] > c->fix[f->cmap[v]]) c->fix[f->cmap[v]] = f->fix[v];
+    }
     L++;
   }
 
@@ -840,8 +913,8 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
   pc = (uint8_t*)malloc((size_t)lv[L].n);
   if (!pc) goto done;
   int32_t trial = -1;
-  if (og_gggp(lv[L].n, lv[L].off, lv[L].adj, lv[L].W, lv[L].vC, lv[L].vG, BC, BG, seed, pc,
-              &trial) != OG_OK)
+  if (og_gggp_fix(lv[L].n, lv[L].off, lv[L].adj, lv[L].W, lv[L].vC, lv[L].vG, lv[L].fix, BC, BG,
+                  seed, pc, &trial) != OG_OK)
     goto done;
 
   /* uncoarsening */
@@ -857,8 +930,8 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
       pc = pf;
       pf = NULL;
     }
-    if (og_refine(lv[l].n, lv[l].off, lv[l].adj, lv[l].W, lv[l].vC, lv[l].vG, BC, BG, pc, &rs) !=
-        OG_OK)
+    if (og_refine_fix(lv[l].n, lv[l].off, lv[l].adj, lv[l].W, lv[l].vC, lv[l].vG, lv[l].fix, BC,
+                      BG, pc, &rs) != OG_OK)
       goto done;
     rounds_total += rs.rounds;
     if (trace) {
@@ -891,6 +964,12 @@ done:
   free(pf);
   for (int l = 0; l <= OG_MAX_LEVELS; l++) og_level_free(&lv[l]);
   return rc;
+}
+
+int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                 const int32_t* cC, const int32_t* cG, double r_cpu, double tol, uint64_t seed,
+                 uint8_t* part, og_result* res, og_trace* trace) {
+  return og_partition_fixed(n, m, off, cols, w, cC, cG, NULL, r_cpu, tol, seed, part, res, trace);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -115,6 +115,16 @@ int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, 
                  const int32_t* cpu_cost, const int32_t* gpu_cost, double r_cpu, double tol,
                  uint64_t seed, uint8_t* part, og_result* res, og_trace* trace);
 
+/* og_partition with fixed vertices (a project addition after Sec. III.B, where every initial kernel
+ * depends on an empty kernel whose data sit in host memory): fixed[v] = 0 pins v to the CPU, 1 to the
+ * GPU, -1 leaves it free (other values: OG_ERR_INVALID); NULL = all free, i.e. og_partition.  Vertices
+ * pinned to different sides never merge, a coarse vertex is pinned where a member is, the growing
+ * starts from the pinned split and moves free vertices only, and refinement never moves a pinned
+ * vertex, so part[v] = fixed[v] wherever fixed[v] >= 0. */
+int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* cols,
+                       const int32_t* w, const int32_t* cC, const int32_t* cG, const int8_t* fixed,
+                       double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
+                       og_trace* trace);
 int og_cut(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* w,
            const uint8_t* part, int64_t* cut);
 

@@ -395,6 +395,30 @@ def from_edges(n: int, edges, cpu_cost, gpu_cost, edge_cost):
                  np.array(gpu_cost, dtype=np.int64), kind="explicit")
 
 
+def with_host_source(g, seed: int, wmax: int = 10000):
+    """The DAG with the paper's host vertex added (Sec. III.B): every kernel without a predecessor
+    gets an edge from one empty kernel (CPU and GPU time 0) that stands for the initial data in host
+    memory.  The new vertex is ``n`` (the last id); its edges' transfer times are U{1..wmax} ns
+    (stream 40).  Returns (graph, source id)."""
+    n, m = int(g["n"]), int(g["m"])
+    off = np.asarray(g["offsets"], dtype=np.int64)
+    cols = np.asarray(g["cols"], dtype=np.int32)
+    indeg = np.bincount(cols, minlength=n) if m else np.zeros(n, np.int64)
+    roots = np.flatnonzero(indeg == 0).astype(np.int32)
+    k = roots.shape[0]
+    offsets = np.empty(n + 2, dtype=np.int64)
+    offsets[: n + 1] = off
+    offsets[n + 1] = m + k
+    w = np.concatenate([np.asarray(g["edge_cost"], dtype=np.int32),
+                        randint(seed, 40, 0, k, 1, wmax).astype(np.int32)])
+    cpu = np.concatenate([np.asarray(g["cpu_cost"], dtype=np.int32), np.zeros(1, np.int32)])
+    gpu = np.concatenate([np.asarray(g["gpu_cost"], dtype=np.int32), np.zeros(1, np.int32)])
+    meta = {k2: v for k2, v in g.items() if k2 not in ("n", "m", "offsets", "cols", "edge_cost", "cpu_cost",
+                                                      "gpu_cost")}
+    meta["host_source"] = n
+    return _pack(n + 1, offsets, np.concatenate([cols, roots]), w, cpu, gpu, **meta), n
+
+
 # --------------------------------------------------------------------------
 # Workload recipes.
 # --------------------------------------------------------------------------

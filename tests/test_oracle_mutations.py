@@ -27,8 +27,8 @@ MUTATIONS = {
     "match_not_mutual": ("if (u >= 0 && pick[u] == (int32_t)v) mate[v] = u;", "if (u >= 0) mate[v] = u;"),
     "match_ignores_cpu_cap": ("if (vC[v] + vC[u] > capC || vG[v] + vG[u] > capG) continue;",
                               "if (vG[v] + vG[u] > capG) continue;"),
-    "twohop_ignores_caps": ("if (pending >= 0 && vC[pending] + vC[v] <= capC && vG[pending] + vG[v] <= capG) {",
-                            "if (pending >= 0) {"),
+    "twohop_ignores_caps": ("if (pending >= 0 && vC[pending] + vC[v] <= capC && vG[pending] + vG[v] <= capG &&",
+                            "if (pending >= 0 &&"),
     "contract_no_weight_sum": ("      cvC[c] += vC[x];", "      cvC[c] = vC[x];"),
     "contract_keeps_self": ("        if (t == c) continue;\n", ""),
     "gain_sign_flipped": ("    gain[v] = ext - in;", "    gain[v] = in - ext;"),
@@ -41,8 +41,19 @@ MUTATIONS = {
     "gggp_worst_trial": ("(feas == best_feas && cut < best_cut)", "(feas == best_feas && cut > best_cut)"),
     "cut_counts_internal": ("if (part[u] != part[cols[e]]) c += w[e];", "if (part[u] == part[cols[e]]) c += w[e];"),
     "stall_rule_inverted": ("if (nc * OG_STALL_DEN > f->n * OG_STALL_NUM) {", "if (nc * OG_STALL_DEN < f->n * OG_STALL_NUM) {"),
-    "no_twohop_in_pipeline": ("        og_match_twohop(f->n, f->off, f->adj, f->W, f->vC, f->vG, capC, capG, seed, mate) != OG_OK) {",
-                              "        0) {"),
+    "fixed_match_ignores_pins": ("        if (!og_compatible(fix, v, u)) continue;\n", ""),
+    "fixed_twohop_ignores_pins": (" &&\n          og_compatible(fix, pending, v)) {", ") {"),
+    "fixed_coarse_pin_lost": ("if (f->fix[v] > c->fix[f->cmap[v]])", "if (f->fix[v] < c->fix[f->cmap[v]])"),
+    "fixed_grow_moves_pins": ("if (side[v] != 1 || (fix && fix[v] >= 0) || LC + vC[v] > BC) continue;",
+                              "if (side[v] != 1 || LC + vC[v] > BC) continue;"),
+    "fixed_grow_start_pinned": ("const int start_free = !fix || fix[start] < 0;", "const int start_free = 1;"),
+    "fixed_refine_moves_pins": ("if (part[v] == src && gain[v] > 0 && !(fix && fix[v] >= 0)) {",
+                                "if (part[v] == src && gain[v] > 0) {"),
+    "fixed_balance_moves_pins": ("if (part[v] == s && !(fix && fix[v] >= 0)) {", "if (part[v] == s) {"),
+    "fixed_grow_region_empty": ("    side[v] = (fix && fix[v] == 0) ? 0 : 1;\n    toC[v] = 0;",
+                                "    side[v] = 1;\n    toC[v] = 0;"),
+    "no_twohop_in_pipeline": ("        og_match_twohop_fix(f->n, f->off, f->adj, f->W, f->vC, f->vG, f->fix, capC, capG, seed,\n"
+                              "                            mate) != OG_OK) {", "        0) {"),
 }
 
 

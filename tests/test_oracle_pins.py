@@ -477,6 +477,111 @@ def test_partition_degenerate_inputs(oracle_mod):
     assert res["feasible"] == 1 and res["cut"] == 0
 
 
+# ---------------------------------------------------------------------------
+# Fixed vertices (the host-source kernel of Sec. III.B pinned to the CPU)
+# ---------------------------------------------------------------------------
+
+def _random_pins(n, seed, frac):
+    """int8 pins: about frac of the vertices pinned, half to each side (stream of its own)."""
+    r = gen.u64(seed, 41, 0, n)
+    fx = np.full(n, -1, np.int8)
+    sel = (r % np.uint64(1000)).astype(np.int64) < int(frac * 1000)
+    fx[sel] = ((r[sel] >> np.uint64(20)) & np.uint64(1)).astype(np.int8)
+    return fx
+
+
+def test_fixed_partition_vs_exhaustive_search(oracle_mod):
+    """Tiny DAGs with one to three pinned vertices: pins hold, the reported cut and loads are the
+    returned split's, and a feasible answer never beats the optimum over the splits that respect
+    the pins (exhaustive); the heuristic is optimal on a good share of instances."""
+    ratios = []
+    for seed in range(90):
+        n = 8 + seed % 10
+        g = gen.two_input_dag(n, seed, extra=seed % 4)
+        fx = np.full(n, -1, np.int8)
+        picks = [int(x) for x in gen.u64(seed, 42, 0, 3) % np.uint64(n)]
+        for i, v in enumerate(picks[: 1 + seed % 3]):
+            fx[v] = (seed + i) & 1
+        part, res = oracle_mod.partition(g, seed=seed, fixed=fx)
+        assert np.all(part[fx >= 0] == fx[fx >= 0])
+        masks, lc, lg, cut = _brute.all_splits(g)
+        mask = int(sum(int(part[v]) << v for v in range(n)))
+        assert res["cut"] == int(cut[mask])
+        assert res["load_cpu"] == int(lc[mask]) and res["load_gpu"] == int(lg[mask])
+        respect = np.ones(masks.shape[0], bool)
+        for v in np.flatnonzero(fx >= 0):
+            respect &= ((masks >> int(v)) & 1) == int(fx[v])
+        ok = respect & (lc <= res["bound_cpu"]) & (lg <= res["bound_gpu"])
+        if ok.any() and res["feasible"]:
+            opt = int(cut[ok].min())
+            assert res["cut"] >= opt
+            ratios.append(res["cut"] / max(opt, 1))
+    r = np.array(ratios)
+    assert len(r) > 60
+    assert (r <= 1.0).mean() >= 0.3 and np.median(r) <= 1.15
+
+
+def test_fixed_all_free_is_the_plain_partition(oracle_mod):
+    for g in (gen.cholesky(12), gen.lu(9), gen.layered(30, 60, 6000, 5)):
+        a = oracle_mod.partition(g, trace=True, seed=3)
+        b = oracle_mod.partition(g, trace=True, seed=3, fixed=np.full(g["n"], -1, np.int8))
+        assert np.array_equal(a[0], b[0]) and a[1] == b[1] and a[2] == b[2]
+
+
+def test_fixed_vertices_keep_their_side_through_every_level(oracle_mod):
+    """Heavy pinning (adjacent vertices pinned to opposite sides are common) on graphs that coarsen
+    over several levels: every pinned vertex ends on its side, the reported loads are the split's."""
+    cases = [(gen.layered(40, 60, 9000, s), s) for s in range(3)] + [(gen.cholesky(14), 7), (gen.lu(10), 8)]
+    for g, s in cases:
+        for frac in (0.05, 0.3, 0.6):
+            fx = _random_pins(g["n"], s * 10 + int(frac * 10), frac)
+            part, res, tr = oracle_mod.partition(g, trace=True, seed=s, fixed=fx)
+            assert tr["levels"] >= 1
+            assert np.all(part[fx >= 0] == fx[fx >= 0]), (s, frac)
+            lc = int(g["cpu_cost"][part == 0].sum())
+            lg = int(g["gpu_cost"][part == 1].sum())
+            assert (res["load_cpu"], res["load_gpu"]) == (lc, lg)
+            assert res["cut"] == oracle_mod.cut(g, part)
+
+
+def test_fixed_host_source_on_the_cpu(oracle_mod):
+    """Sec. III.B: the initial data sit in host memory, modelled as an empty kernel feeding every
+    kernel without a predecessor.  Pinned, it stays on the CPU; its zero costs change no load.
+    With a large speed gap everything free goes to the GPU with the source alone on the CPU: the
+    growing's pre-check (trial -1), which refinement can only improve on."""
+    base = gen.layered(20, 50, 3000, 1)
+    g, src = gen.with_host_source(base, 1)
+    fx = np.full(g["n"], -1, np.int8)
+    fx[src] = 0
+    part, res, tr = oracle_mod.partition(g, trace=True, fixed=fx)
+    assert part[src] == 0
+    assert np.flatnonzero(np.bincount(g["cols"], minlength=g["n"]) == 0).tolist() == [src]
+    roots = np.flatnonzero(np.bincount(base["cols"], minlength=base["n"]) == 0)
+    assert g["cols"][g["offsets"][src]:].tolist() == roots.tolist() and len(roots) >= 50
+    gap, s2 = gen.with_host_source(gen.random_dag(60, 150, 2, ratio_pct=(1, 3)), 2)
+    fx = np.full(gap["n"], -1, np.int8)
+    fx[s2] = 0
+    part, res, tr = oracle_mod.partition(gap, trace=True, fixed=fx)
+    assert tr["gggp_trial"] == -1 and part[s2] == 0 and res["feasible"] == 1
+    # refinement starts from that split and only lowers its cut (the source's transfers)
+    off = gap["offsets"]
+    assert res["cut"] <= int(gap["edge_cost"][off[s2]:off[s2 + 1]].sum())
+    assert (part == 0).sum() <= 3
+
+
+def test_fixed_everything_pinned_and_bad_values(oracle_mod):
+    g = gen.cholesky(8)
+    for s in range(4):
+        fx = (gen.u64(s, 43, 0, g["n"]) & np.uint64(1)).astype(np.int8)
+        part, res = oracle_mod.partition(g, fixed=fx, seed=s)
+        assert np.array_equal(part, fx.astype(np.uint8))
+        assert res["feasible"] == int(res["load_cpu"] <= res["bound_cpu"] and res["load_gpu"] <= res["bound_gpu"])
+    bad = np.full(g["n"], -1, np.int8)
+    bad[5] = 2
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.partition(g, fixed=bad)
+
+
 def test_validation_codes(oracle_mod):
     ok = gen.from_edges(3, [(0, 1), (1, 2)], [1, 1, 1], [1, 1, 1], [1, 1])
     assert oracle_mod.validate(ok) == oracle_mod.OK
