@@ -493,6 +493,9 @@ def main():
                    "sample": "the full workload, one partition + makespan (%.1f s)" % dt}
             bit_exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == res["cut"] and oms == ms)
 
+    fixed = None
+    if not big:
+        fixed = bench_fixed(g, K, W, stream, flush, with_oracle=not args.no_cpu_baseline)
     learned = None
     if not args.no_learned:
         learned = bench_learned(g, dg, part, res, ms, K, W, stream, flush, bgen.held_out() if bgen else [])
@@ -534,9 +537,70 @@ def main():
         line["batch"] = batch
     if learned:
         line["learned"] = learned
+    if fixed:
+        line["fixed"] = fixed
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_fixed(g, K, W, stream, flush, with_oracle):
+    """The workload with the paper's host vertex (Sec. III.B: an empty kernel, holding the initial
+    data in host memory, feeds every kernel without a predecessor) pinned to the CPU, through
+    gp_partition_fixed; the same step as the plain line (deferred create + partition + makespan +
+    destroy), K steps after W warm-ups, L2 flushed between steps.  Also: where the plain path puts
+    that vertex, and (unless the CPU baseline is off) bit-exactness against the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1502_07451_b300 as gp
+    from paper_1502_07451_b300 import gen
+    hs, src = gen.with_host_source(g, 0)
+    n, m = hs["n"], hs["m"]
+    keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
+    dg = {k: torch.from_numpy(hs[k]).cuda() for k in keys}
+    fx = np.full(n, -1, np.int8)
+    fx[src] = 0
+    dfx = torch.from_numpy(fx).cuda()
+    part = torch.empty(n, dtype=torch.uint8, device="cuda")
+
+    def step():
+        h = gp.gp_graph_create_deferred(n, m, dg["offsets"], dg["cols"], dg["edge_cost"], dg["cpu_cost"],
+                                        dg["gpu_cost"], stream=stream)
+        r = gp.gp_partition_fixed(h, dfx, -1.0, 0.03, 0, part, stream)
+        mk = gp.gp_makespan(h, part, None, stream)
+        gp.gp_graph_destroy(h)
+        return r, mk
+
+    for _ in range(W):
+        res, mk = step()
+    torch.cuda.synchronize()
+    total = 0.0
+    for _ in range(K):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        res, mk = step()
+        b.record(stream)
+        b.synchronize()
+        total += a.elapsed_time(b)
+    p = part.cpu().numpy()
+    # the same graph without the pin
+    h = gp.gp_graph_create(n, m, *[dg[k] for k in keys], stream=stream)
+    free_part = torch.empty_like(part)
+    rfree = gp.gp_partition(h, -1.0, 0.03, 0, free_part, stream)
+    gp.gp_graph_destroy(h)
+    out = {"workload": "the layered DAG above plus the host vertex feeding its %d kernels without a predecessor "
+                       "(%d vertices, %d edges), pinned to the CPU" % (m - g["m"], n, m),
+           "entry": "gp_partition_fixed", "metric": METRIC, "value": K * m / (total / 1e3), "unit": UNIT,
+           "ms_per_step": total / K, "cut": res["cut"], "feasible": res["feasible"], "makespan_ns": mk,
+           "host_vertex_on_cpu": bool(p[src] == 0),
+           "without_pin": {"cut": rfree["cut"], "host_vertex_side": int(free_part[src].item())}}
+    if with_oracle:
+        opart, ores = oracle.partition(hs, fixed=fx)
+        out["bit_exact_vs_oracle"] = bool(np.array_equal(opart, p) and ores["cut"] == res["cut"]
+                                          and ores["load_cpu"] == res["load_cpu"])
+    return out
 
 
 def bench_learned(g, dg, part_plain, res_plain, ms_plain, K, W, stream, flush, held_out):

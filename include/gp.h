@@ -167,6 +167,22 @@ GP_API gp_status gp_bounds(int64_t sum_cpu, int64_t sum_gpu, double r_cpu, doubl
 GP_API gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uint8_t* part_out,
                        gp_result* res, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * gp_partition_fixed -- gp_partition with fixed vertices.  Sec. III.B roots every initial kernel at
+ * an empty kernel whose data sit in host memory; that vertex belongs on the CPU whatever the split.
+ *   fixed     int8[n], host or device: 0 pins the vertex to the CPU, 1 to the GPU, -1 leaves it
+ *             free; NULL = every vertex free (then exactly gp_partition)
+ * Vertices pinned to different sides never merge while coarsening (a coarse vertex is pinned where
+ * a member is), the growing starts from the pinned split and moves free vertices only (its all-GPU
+ * pre-check becomes: every free vertex on the GPU), and refinement never moves a pinned vertex; so
+ * part_out[v] = fixed[v] wherever fixed[v] >= 0.  Pinned loads count toward the bounds: a split
+ * they make infeasible returns GP_OK with res->feasible = 0.  The array is read during the call
+ * only (the caller keeps it).  Errors: those of gp_partition; GP_ERR_INVALID for a value outside
+ * {-1, 0, 1}.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_partition_fixed(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
+                             uint8_t* part_out, gp_result* res, void* stream);
+
 /* Per-level record of the last gp_partition call on g (host struct). */
 GP_API gp_status gp_last_trace(const gp_graph* g, gp_trace* trace);
 

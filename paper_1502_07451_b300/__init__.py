@@ -84,6 +84,7 @@ def lib():
                 "gp_graph_export": [_P, _P, _P, _P, _P, _P],
                 "gp_bounds": [_I64, _I64, _D, _D, _P, _P],
                 "gp_partition": [_P, _D, _D, _U64, _P, _P, _P],
+                "gp_partition_fixed": [_P, _P, _D, _D, _U64, _P, _P, _P],
                 "gp_last_trace": [_P, _P],
                 "gp_makespan": [_P, _P, _P, _P, _P],
                 "gp_cut": [_P, _P, _P, _P],
@@ -257,6 +258,17 @@ def gp_partition(h, r_cpu, tol, seed, part_out, stream=None):
     res = Result()
     _check(lib().gp_partition(h, float(r_cpu), float(tol), int(seed), _ptr(part_out)[0], C.byref(res),
                               _stream(stream)), "gp_partition")
+    return res.as_dict()
+
+
+def gp_partition_fixed(h, fixed, r_cpu, tol, seed, part_out, stream=None):
+    """gp_partition with pinned vertices: fixed = int8 per vertex (0 CPU, 1 GPU, -1 free), host or
+    device, or None (all free)."""
+    if fixed is not None and str(getattr(fixed, "dtype", "")) not in ("int8", "torch.int8"):
+        raise TypeError("fixed must be an int8 array")
+    res = Result()
+    _check(lib().gp_partition_fixed(h, _ptr(fixed)[0], float(r_cpu), float(tol), int(seed), _ptr(part_out)[0],
+                                    C.byref(res), _stream(stream)), "gp_partition_fixed")
     return res.as_dict()
 
 
@@ -524,7 +536,9 @@ class Graph:
     def info(self):
         return gp_graph_info(self.h)
 
-    def partition(self, part_out, r_cpu=-1.0, tol=0.03, seed=0, stream=None):
+    def partition(self, part_out, r_cpu=-1.0, tol=0.03, seed=0, stream=None, fixed=None):
+        if fixed is not None:
+            return gp_partition_fixed(self.h, fixed, r_cpu, tol, seed, part_out, stream)
         return gp_partition(self.h, r_cpu, tol, seed, part_out, stream)
 
     def makespan(self, part, finish_out=None, stream=None):

@@ -845,8 +845,8 @@ struct TraceDev {
   Ctl ctl;
 };
 
-gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uint8_t* part_out, gp_result* res,
-                       void* stream) {
+static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
+                                uint8_t* part_out, gp_result* res, void* stream) {
   if (!g || (!part_out && g->n > 0)) return GP_ERR_INVALID;
   int64_t BC, BG;
   gp_status st = host_bounds(g->SC, g->SG, r_cpu, tol, &BC, &BG);
@@ -893,6 +893,17 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
       int64_t* p;
       ~SlotGuard() { pinned_slot_free(p); }
     } slot_guard{hbuf};
+    if (fixed) {  // pinned vertices: a device copy, checked before any level uses it
+      int8_t* fx = A.get<int8_t>(n);
+      int* bad = A.get<int>(1);
+      GP_CUDA(cudaMemcpyAsync(fx, fixed, (size_t)n, cudaMemcpyDefault, s));
+      GP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+      GP_LAUNCH(F_MISC, k_fix_check, grid_for(n, 256), 256, 0, s, n, (const int8_t*)fx, bad);
+      GP_CUDA(cudaMemcpyAsync(hbuf, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+      GP_CUDA(cudaStreamSynchronize(s));
+      if (*(int*)hbuf) throw Fail{GP_ERR_INVALID};
+      L[0].fix = fx;
+    }
     int lev = 0;
     auto take_entries = [&](int l) {  // level l's entries, copied to hbuf[1] before the last sync
       L[l].a = hbuf[1];
@@ -929,6 +940,7 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
       A.ptrs.push_back(c.W);
       A.ptrs.push_back(c.vC);
       A.ptrs.push_back(c.vG);
+      if (c.fix) A.ptrs.push_back(c.fix);
       GP_LAUNCH(F_MISC, k_sum_deg, grid_for(nc, 256, 8), 256, 0, s, (int64_t)nc, c.deg, adev + lev + 1);
       cmaps.push_back(cmap);
       c.a = 0;  // taken at the next level's round trip
@@ -1045,6 +1057,16 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
     cudaGetLastError();
     return f.st;
   }
+}
+
+gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uint8_t* part_out, gp_result* res,
+                       void* stream) {
+  return partition_impl(g, nullptr, r_cpu, tol, seed, part_out, res, stream);
+}
+
+gp_status gp_partition_fixed(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
+                             uint8_t* part_out, gp_result* res, void* stream) {
+  return partition_impl(g, fixed, r_cpu, tol, seed, part_out, res, stream);
 }
 
 gp_status gp_last_trace(const gp_graph* g, gp_trace* trace) {

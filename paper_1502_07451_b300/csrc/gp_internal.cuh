@@ -236,6 +236,7 @@ struct LevelGraph {
   int64_t* W = nullptr;
   int64_t* vC = nullptr;
   int64_t* vG = nullptr;
+  int8_t* fix = nullptr;  // fixed vertices: 0 pinned to the CPU, 1 to the GPU, -1 free; null: none
 };
 
 // ------------------------------------------------------------------------------------------------

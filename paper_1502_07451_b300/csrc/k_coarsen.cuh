@@ -9,6 +9,8 @@
 // pending).  Contraction: representatives (unmatched vertices and the smaller end of each pair)
 // are numbered in vertex order; a coarse row is the union of both members' rows mapped through
 // cmap, without the coarse vertex itself, equal neighbours added up.
+// Fixed vertices (g.fix non-null): two vertices pinned to different sides never merge, in either
+// step; a coarse vertex is pinned where one of its members is.
 #pragma once
 #include "gp_internal.cuh"
 #include "k_graph.cuh"
@@ -96,8 +98,9 @@ struct LazyKey {
 
 // One handshake round, picks: a group of G lanes per unmatched vertex.  `tid` / `stride`: the
 // calling thread and the number of threads sharing the level (grid or one CTA).  Returns, per
-// thread, whether it recorded a pick.
-template <int G>
+// thread, whether it recorded a pick.  FIX: g.fix is set (a separate instance: the check costs the
+// plain picks 10 registers).
+template <int G, bool FIX = false>
 __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, long long mC, long long mG,
                            const int32_t* __restrict__ mate, int32_t* __restrict__ pick,
                            uint8_t* __restrict__ alive, int64_t tid, int64_t stride, bool all_free = false) {
@@ -114,6 +117,7 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
     const int32_t d = g.deg[v];
     const int64_t cv = g.vC[v], gv = g.vG[v];
     const bool nocap = cv + mC <= capC && gv + mG <= capG;
+    const int8_t fv = FIX ? g.fix[v] : (int8_t)-1;  // a free v is compatible with every neighbour
     LazyKey lk;
     // four entries per lane in flight: ids and weights, then the neighbours' match state
     for (int32_t k0 = sub; k0 < d; k0 += 4 * G) {
@@ -141,6 +145,15 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
           ok[q] = cv + g.vC[us[q]] <= capC && gv + g.vG[us[q]] <= capG;
         }
       }
+      if (FIX && fv >= 0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+          if (!ok[q]) continue;
+          bytes += 1;
+          const int8_t fu = g.fix[us[q]];
+          ok[q] = fu < 0 || fu == fv;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < 4; q++)
         if (ok[q]) lk.offer(ws[q], (uint32_t)us[q], seed, (uint32_t)v);
@@ -160,12 +173,12 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
   account(F_MATCH_PICK, bytes, sacc);
   return picked;
 }
-template <int G>
+template <int G, bool FIX>
 __global__ void __launch_bounds__(256)
     k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const long long* __restrict__ maxw,
                  const int32_t* __restrict__ mate, int32_t* __restrict__ pick, uint8_t* __restrict__ alive,
                  int all_free) {
-  match_pick<G>(g, capC, capG, seed, maxw[0], maxw[1], mate, pick, alive,
+  match_pick<G, FIX>(g, capC, capG, seed, maxw[0], maxw[1], mate, pick, alive,
                 (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, all_free != 0);
 }
 
@@ -260,16 +273,19 @@ __device__ void pair_sorted(const LevelGraph& g, int64_t capC, int64_t capG, con
   const unsigned lt = lanemask_lt();
   int32_t p_id = -1;  // carried last item
   int64_t p_c = 0, p_g = 0;
+  int p_f = -1;
   bool p_pend = false;
   for (int64_t base = 0; base < nitems; base += 32) {
     const bool flag = base + lane < nitems;
     const int32_t v = flag ? items[base + lane] : -1;
     const unsigned m = __ballot_sync(0xffffffffu, flag);
     int64_t vc = 0, vg = 0;
+    int vf = -1;
     if (flag) {
       vc = g.vC[v];
       vg = g.vG[v];
       bytes += 20;
+      if (g.fix) vf = g.fix[v];
     }
     const unsigned below = m & lt;
     const int pred_lane = below ? 31 - __clz(below) : -1;
@@ -277,12 +293,15 @@ __device__ void pair_sorted(const LevelGraph& g, int64_t capC, int64_t capG, con
     int32_t q_id = __shfl_sync(0xffffffffu, v, srcl);
     int64_t q_c = __shfl_sync(0xffffffffu, vc, srcl);
     int64_t q_g = __shfl_sync(0xffffffffu, vg, srcl);
+    int q_f = __shfl_sync(0xffffffffu, vf, srcl);
     if (pred_lane < 0) {
       q_id = p_id;
       q_c = p_c;
       q_g = p_g;
+      q_f = p_f;
     }
-    const bool okprev = flag && q_id >= 0 && (q_c + vc <= capC) && (q_g + vg <= capG);
+    const bool okprev = flag && q_id >= 0 && (q_c + vc <= capC) && (q_g + vg <= capG) &&
+                        (q_f < 0 || vf < 0 || q_f == vf);
     const int sidx = __popc(below);
     int scan = (flag && !okprev) ? sidx : INT_MIN;
 #pragma unroll
@@ -302,6 +321,7 @@ __device__ void pair_sorted(const LevelGraph& g, int64_t capC, int64_t capG, con
     p_id = __shfl_sync(0xffffffffu, v, last);
     p_c = __shfl_sync(0xffffffffu, vc, last);
     p_g = __shfl_sync(0xffffffffu, vg, last);
+    p_f = __shfl_sync(0xffffffffu, vf, last);
     p_pend = __shfl_sync(0xffffffffu, P, last);
   }
 }
@@ -558,7 +578,8 @@ __global__ void k_rep_flags(int64_t n, const int32_t* __restrict__ mate, uint8_t
 // vertices: members, summed weights, raw row length.
 __device__ void cmap_fill(const LevelGraph& g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
                           int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of, int64_t* __restrict__ cvC,
-                          int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen, int64_t tid, int64_t stride) {
+                          int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen, int64_t tid, int64_t stride,
+                          int8_t* __restrict__ cfix = nullptr) {
   for (int64_t v = tid; v < g.n; v += stride) {
     const int32_t u = mate[v];
     if (u < 0 || v < u) {
@@ -567,6 +588,10 @@ __device__ void cmap_fill(const LevelGraph& g, const int32_t* __restrict__ mate,
       mate_of[c] = u;
       cvC[c] = g.vC[v] + (u >= 0 ? g.vC[u] : 0);
       cvG[c] = g.vG[v] + (u >= 0 ? g.vG[u] : 0);
+      if (cfix) {  // members are compatible: at most one side among them
+        const int8_t a = g.fix[v], b = u >= 0 ? g.fix[u] : (int8_t)-1;
+        cfix[c] = a > b ? a : b;
+      }
       rawlen[c] = (int64_t)g.deg[v] + (u >= 0 ? (int64_t)g.deg[u] : 0);
     } else {
       cmap[v] = cmap[u];
@@ -575,9 +600,10 @@ __device__ void cmap_fill(const LevelGraph& g, const int32_t* __restrict__ mate,
 }
 __global__ void k_cmap_fill(LevelGraph g, const int32_t* __restrict__ mate, int32_t* __restrict__ cmap,
                             int32_t* __restrict__ rep_of, int32_t* __restrict__ mate_of,
-                            int64_t* __restrict__ cvC, int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen) {
+                            int64_t* __restrict__ cvC, int64_t* __restrict__ cvG, int64_t* __restrict__ rawlen,
+                            int8_t* __restrict__ cfix) {
   cmap_fill(g, mate, cmap, rep_of, mate_of, cvC, cvG, rawlen, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-            (int64_t)gridDim.x * blockDim.x);
+            (int64_t)gridDim.x * blockDim.x, cfix);
 }
 
 static inline unsigned grid_for(int64_t work, int per_block, int max_per_sm = 16) {
@@ -612,8 +638,12 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
     switch (G) {
 #define GP_MP(GG)                                                                                       \
   case GG:                                                                                             \
-    GP_LAUNCH(F_MATCH_PICK, k_match_pick<GG>, grid_for(n * GG, 256), 256, 0, s, g, capC, capG, seed,    \
-              (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0);                              \
+    if (g.fix)                                                                                         \
+      GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, true>), grid_for(n * GG, 256), 256, 0, s, g, capC, capG, \
+                seed, (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0);                        \
+    else                                                                                               \
+      GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, false>), grid_for(n * GG, 256), 256, 0, s, g, capC,      \
+                capG, seed, (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0);                  \
     break;
       GP_MP(2) GP_MP(4) GP_MP(8) GP_MP(16) GP_MP(32)
 #undef GP_MP
@@ -687,8 +717,9 @@ void contract_level(const LevelGraph& g, const int32_t* mate, int32_t* cmap, Lev
   cg.vG = dnew<int64_t>(nc, s);
   cg.adj = dnew<int32_t>(cg.cap, s);
   cg.W = dnew<int64_t>(cg.cap, s);
+  cg.fix = g.fix ? dnew<int8_t>(nc, s) : nullptr;
   GP_LAUNCH(F_CMAP, k_cmap_fill, grid_for(g.n, 256), 256, 0, s, g, mate, cmap, rep_of, mate_of, cg.vC, cg.vG,
-            rawlen);
+            rawlen, cg.fix);
   scan_i64(rawlen, cg.start, nc, s);
   TwoSrc src{};
   src.a_start = g.start;

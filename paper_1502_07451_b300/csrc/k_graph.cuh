@@ -450,4 +450,12 @@ __global__ void k_fill_u8(int64_t n, uint8_t* p, uint8_t x) {
     p[v] = x;
 }
 
+// fixed-vertex values outside {-1, 0, 1} set *bad
+__global__ void k_fix_check(int64_t n, const int8_t* __restrict__ fix, int* bad) {
+  bool b = false;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    b |= fix[v] < -1 || fix[v] > 1;
+  if (__any_sync(0xffffffffu, b) && (threadIdx.x & 31) == 0) *bad = 1;
+}
+
 }  // namespace gp

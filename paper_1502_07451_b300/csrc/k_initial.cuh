@@ -6,6 +6,9 @@
 // is adjacent) and the one with the largest gain W(to CPU) - W(to GPU), smallest id on ties, moves.
 // One CTA runs one trial; each step is a block-wide argmax.  The best trial is the feasible one with
 // the smallest cut, then the smallest t.  All-GPU is chosen without trials when sum vG <= B_G.
+// Fixed vertices (g.fix non-null): the CPU-pinned ones start in the CPU region, only free vertices
+// move, and the pre-check is on the split with every free vertex on the GPU (decided in the kernel:
+// every trial then reports it, flagged 2, and the pick records trial -1).
 #pragma once
 #include "gp_internal.cuh"
 #include "k_coarsen.cuh"
@@ -47,6 +50,7 @@ __global__ void __launch_bounds__(kGggpThreads)
            int32_t* __restrict__ adjC_all, long long* __restrict__ res) {
   __shared__ long long s_LC, s_LG;
   __shared__ int32_t s_x;
+  __shared__ int s_pre;
   __shared__ GrowKey s_best[kGggpThreads / 32];
   __shared__ long long sh[32];
   __shared__ unsigned long long sacc[32];
@@ -58,16 +62,34 @@ __global__ void __launch_bounds__(kGggpThreads)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   unsigned long long bytes = 0;
   for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
-    side[v] = 1;
+    side[v] = (g.fix && g.fix[v] == 0) ? 0 : 1;
     toC[v] = 0;
     adjC[v] = 0;
+  }
+  long long LC0 = 0, LG0 = SG;
+  if (g.fix) {  // the CPU-pinned vertices form the initial region
+    __syncthreads();
+    long long c = 0, gg = 0;
+    for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
+      if (g.fix[v] != 0) continue;
+      c += g.vC[v];
+      gg += g.vG[v];
+      for (int64_t e = g.start[v]; e < g.start[v] + g.deg[v]; e++) {
+        atomicAdd((unsigned long long*)&toC[g.adj[e]], (unsigned long long)g.W[e]);
+        atomicAdd(&adjC[g.adj[e]], 1);
+      }
+    }
+    LC0 = block_sum<long long>(c, sh);
+    LG0 = SG - block_sum<long long>(gg, sh);
   }
   if (threadIdx.x == 0) {
     const int64_t s = start_override >= 0 ? start_override
                                           : (int64_t)(pair_hash(seed, 0xFFFFFFFFu, (uint32_t)t) % (uint64_t)n);
-    s_LC = 0;
-    s_LG = SG;
-    s_x = (g.vC[s] <= BC) ? (int32_t)s : -1;
+    s_LC = LC0;
+    s_LG = LG0;
+    s_pre = g.fix != nullptr && LC0 <= BC && LG0 <= BG;
+    const bool sfree = !g.fix || g.fix[s] < 0;
+    s_x = (!s_pre && sfree && LC0 + g.vC[s] <= BC) ? (int32_t)s : -1;
   }
   __syncthreads();
   for (;;) {
@@ -92,7 +114,7 @@ __global__ void __launch_bounds__(kGggpThreads)
     const long long LC = s_LC;
     GrowKey best{0, 0, -1};
     for (int64_t v = threadIdx.x; v < n; v += blockDim.x) {
-      if (side[v] != 1 || LC + g.vC[v] > BC) continue;
+      if (side[v] != 1 || (g.fix && g.fix[v] >= 0) || LC + g.vC[v] > BC) continue;
       const GrowKey k{adjC[v] > 0 ? 1 : 0, 2 * toC[v] - wsum[v], (int32_t)v};
       if (grow_better(k, best)) best = k;
     }
@@ -122,7 +144,7 @@ __global__ void __launch_bounds__(kGggpThreads)
   cut = block_sum<long long>(cut, sh);
   if (threadIdx.x == 0) {
     res[4 * t + 0] = cut;
-    res[4 * t + 1] = (s_LC <= BC && s_LG <= BG) ? 1 : 0;
+    res[4 * t + 1] = s_pre ? 2 : (s_LC <= BC && s_LG <= BG) ? 1 : 0;
     res[4 * t + 2] = s_LC;
     res[4 * t + 3] = s_LG;
   }
@@ -139,7 +161,7 @@ __global__ void k_gggp_pick(int64_t n, int ntrials, const long long* __restrict_
       if (f > bf || (f == bf && res[4 * t] < res[4 * bt])) bt = t;
     }
     s_t = bt;
-    *trial_out = bt;
+    *trial_out = res[4 * bt + 1] == 2 ? -1 : bt;  // 2: the pre-check's split (every trial holds it)
   }
   __syncthreads();
   const uint8_t* side = side_all + (int64_t)s_t * n;
@@ -152,7 +174,7 @@ void gggp(const LevelGraph& g, int64_t BC, int64_t BG, int64_t SG, uint64_t seed
           cudaStream_t s) {
   const int64_t n = g.n;
   if (n <= 0) return;
-  if (SG <= BG) {
+  if (!g.fix && SG <= BG) {
     GP_LAUNCH(F_GGGP, k_fill_u8, grid_for(n, 256), 256, 0, s, n, part, (uint8_t)1);
     GP_LAUNCH(F_MISC, k_set_i32, 1, 1, 0, s, trial_dev, -1);
     GP_CHECK_LAUNCH();

@@ -211,7 +211,7 @@ __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part,
         bytes += 12;
         if (cand.stamp[v] != prev_tag) {  // stale ones are recomputed below
           gain = cand.gainv[v];
-          want = r < 0 || gain > 0;
+          want = (r < 0 || gain > 0) && !(g.fix && g.fix[v] >= 0);  // a fixed vertex never moves
         }
       }
     }
@@ -249,7 +249,7 @@ __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part,
     if (lane == 0) {
       cand.gainv[v] = acc;
       bytes += 29ull + 13ull * (unsigned long long)d;
-      if (p == src && (r < 0 || acc > 0)) {
+      if (p == src && (r < 0 || acc > 0) && !(g.fix && g.fix[v] >= 0)) {
         push_cand(cc, cand, v, acc, cdst[v], csrc[v], sum_cd, sum_cs, gmax, gmin);
         bytes += 44;
       }
