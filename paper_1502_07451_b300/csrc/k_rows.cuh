@@ -400,11 +400,19 @@ __global__ void __launch_bounds__(kHugeThreads)
 
 // ------------------------------------------------------------------------------------------------
 // Unordered merge (contraction): duplicates are combined in a per-warp shared-memory hash table and
-// the distinct (column, summed weight) pairs are written in table order.  Every consumer of coarse
-// rows is independent of their order (sums, maxima under a total order, sets); the two-hop pairing
-// sorts what it walks.  Rows longer than TMAX / 2 raw entries are deferred to the next tier.
+// the distinct (column, summed weight) pairs are written in no particular order.  Every consumer of
+// coarse rows is independent of their order (sums, maxima under a total order, sets); the two-hop
+// pairing sorts what it walks.  Rows longer than TMAX / 2 raw entries are deferred to the next tier.
+// The table is emptied once per warp; a row's inserts remember the slots they claimed (one per lane
+// and pass, in registers), and after the row only those slots are read out and emptied again, so a
+// row costs work in its distinct entries, not in the table size.
 // ------------------------------------------------------------------------------------------------
 constexpr int32_t kEmptyKey = -1;
+
+template <int TMAX>
+__device__ __forceinline__ int table_shift() {  // slot = (col * golden) >> shift covers [0, TMAX)
+  return 32 - (31 - __clz(TMAX));
+}
 
 template <int TMAX, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
@@ -413,14 +421,21 @@ __global__ void __launch_bounds__(WARPS * 32)
                  int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int32_t* __restrict__ dl1,
                  unsigned* dc1, int64_t split1, int32_t* __restrict__ dl2, unsigned* dc2, int64_t split2,
                  int32_t* __restrict__ dl3, unsigned* dc3, int fam) {
+  constexpr int kPasses = TMAX / 64;  // a row holds at most TMAX / 2 raw entries, 32 per pass
   extern __shared__ __align__(16) unsigned char smem_h[];
   __shared__ unsigned long long sacc[32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   unsigned long long* V = (unsigned long long*)smem_h + (size_t)wib * TMAX;
   int32_t* K = (int32_t*)((unsigned long long*)smem_h + (size_t)WARPS * TMAX) + (size_t)wib * TMAX;
   const unsigned lt = lanemask_lt();
+  const int shift = table_shift<TMAX>();
   const int64_t total = list ? (int64_t)*list_cnt : nrows;
   unsigned long long bytes = 0;
+  for (int i = lane; i < TMAX; i += 32) {
+    K[i] = kEmptyKey;
+    V[i] = 0ull;
+  }
+  __syncwarp();
   for (int64_t it = (int64_t)blockIdx.x * WARPS + wib; it < total; it += (int64_t)gridDim.x * WARPS) {
     const int64_t r = list ? (int64_t)list[it] : it;
     const RowView v = row_view(s, r);
@@ -436,41 +451,46 @@ __global__ void __launch_bounds__(WARPS * 32)
       }
       continue;
     }
-    int T = 32;
-    while (T < 2 * len) T <<= 1;
-    const int shift = 32 - (31 - __clz(T));
-    for (int i = lane; i < T; i += 32) {
-      K[i] = kEmptyKey;
-      V[i] = 0ull;
-    }
-    __syncwarp();
-    for (int64_t i = lane; i < len; i += 32) {
+    int slot[kPasses];
+    unsigned claimed = 0;  // bit p: this lane's entry of pass p took a new slot
+#pragma unroll
+    for (int p = 0; p < kPasses; p++) {
+      slot[p] = 0;
+      if (p * 32 >= len) break;
+      const int64_t i = p * 32 + lane;
+      if (i >= len) continue;
       int32_t col;
       int64_t w;
       row_entry(s, v, i, col, w);
       bytes += entry_bytes(s, i < v.a_len);
       if (s.drop_self && col == (int32_t)r) continue;
-      unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+      unsigned sl = ((uint32_t)col * 0x9E3779B1u) >> shift;
       for (;;) {
-        const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+        const int32_t old = atomicCAS(&K[sl], kEmptyKey, col);
         if (old == kEmptyKey || old == col) {
-          atomicAdd(&V[slot], (unsigned long long)w);
+          atomicAdd(&V[sl], (unsigned long long)w);
+          if (old == kEmptyKey) claimed |= 1u << p;
           break;
         }
-        slot = (slot + 1) & (unsigned)(T - 1);
+        sl = (sl + 1) & (unsigned)(TMAX - 1);
       }
+      slot[p] = (int)sl;
     }
     __syncwarp();
+    // each distinct column is read out (and its slot emptied) by the lane that claimed its slot
     const int64_t ob = out_start[r];
     int out = 0;
-    for (int base = 0; base < T; base += 32) {
-      const int32_t k = K[base + lane];
-      const bool has = k != kEmptyKey;
-      const unsigned m = __ballot_sync(0xffffffffu, has);
-      if (has) {
+#pragma unroll
+    for (int p = 0; p < kPasses; p++) {
+      if (p * 32 >= len) break;
+      const bool c = (claimed >> p) & 1u;
+      const unsigned m = __ballot_sync(0xffffffffu, c);
+      if (c) {
         const int pos = out + __popc(m & lt);
-        adj_out[ob + pos] = k;
-        W_out[ob + pos] = (int64_t)V[base + lane];
+        adj_out[ob + pos] = K[slot[p]];
+        W_out[ob + pos] = (int64_t)V[slot[p]];
+        K[slot[p]] = kEmptyKey;
+        V[slot[p]] = 0ull;
       }
       out += __popc(m);
     }
@@ -564,10 +584,13 @@ __global__ void __launch_bounds__(256)
 
 // Block per row: one hash table over the block's dynamic shared memory (TMAX entries), rows of up to
 // TMAX / 2 raw entries, taken from `list`; output positions come from a block counter (any order).
-template <int TMAX>
-__global__ void k_merge_hash_blk(TwoSrc s, const int32_t* __restrict__ list, const unsigned* list_cnt,
-                                 const int64_t* __restrict__ out_start, int32_t* __restrict__ deg_out,
-                                 int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int fam) {
+// As in the warp tier, the table is emptied once and each row empties the slots it claimed.
+template <int TMAX, int THREADS>
+__global__ void __launch_bounds__(THREADS)
+    k_merge_hash_blk(TwoSrc s, const int32_t* __restrict__ list, const unsigned* list_cnt,
+                     const int64_t* __restrict__ out_start, int32_t* __restrict__ deg_out,
+                     int32_t* __restrict__ adj_out, int64_t* __restrict__ W_out, int fam) {
+  constexpr int kPasses = TMAX / 2 / THREADS;
   extern __shared__ __align__(16) unsigned char smem_b[];
   __shared__ unsigned long long sacc[32];
   __shared__ unsigned s_out;
@@ -575,50 +598,61 @@ __global__ void k_merge_hash_blk(TwoSrc s, const int32_t* __restrict__ list, con
   int32_t* K = (int32_t*)(V + TMAX);
   const int lane = threadIdx.x & 31;
   const unsigned lt = lanemask_lt();
+  const int shift = table_shift<TMAX>();
   const int64_t total = (int64_t)*list_cnt;
   unsigned long long bytes = 0;
+  if (total <= (int64_t)blockIdx.x) return;  // no row for this block (uniform)
+  for (int i = threadIdx.x; i < TMAX; i += THREADS) {
+    K[i] = kEmptyKey;
+    V[i] = 0ull;
+  }
   for (int64_t it = blockIdx.x; it < total; it += gridDim.x) {
     const int64_t r = list[it];
     const RowView v = row_view(s, r);
     const int64_t len = v.a_len + v.b_len;
-    int T = 64;
-    while (T < 2 * len) T <<= 1;
-    const int shift = 32 - (31 - __clz(T));
-    for (int i = threadIdx.x; i < T; i += blockDim.x) {
-      K[i] = kEmptyKey;
-      V[i] = 0ull;
-    }
     if (threadIdx.x == 0) s_out = 0;
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+    int slot[kPasses];
+    unsigned claimed = 0;
+#pragma unroll
+    for (int p = 0; p < kPasses; p++) {
+      slot[p] = 0;
+      if ((int64_t)p * THREADS >= len) break;
+      const int64_t i = (int64_t)p * THREADS + threadIdx.x;
+      if (i >= len) continue;
       int32_t col;
       int64_t w;
       row_entry(s, v, i, col, w);
       bytes += entry_bytes(s, i < v.a_len);
       if (s.drop_self && col == (int32_t)r) continue;
-      unsigned slot = ((uint32_t)col * 0x9E3779B1u) >> shift;
+      unsigned sl = ((uint32_t)col * 0x9E3779B1u) >> shift;
       for (;;) {
-        const int32_t old = atomicCAS(&K[slot], kEmptyKey, col);
+        const int32_t old = atomicCAS(&K[sl], kEmptyKey, col);
         if (old == kEmptyKey || old == col) {
-          atomicAdd(&V[slot], (unsigned long long)w);
+          atomicAdd(&V[sl], (unsigned long long)w);
+          if (old == kEmptyKey) claimed |= 1u << p;
           break;
         }
-        slot = (slot + 1) & (unsigned)(T - 1);
+        sl = (sl + 1) & (unsigned)(TMAX - 1);
       }
+      slot[p] = (int)sl;
     }
     __syncthreads();
     const int64_t ob = out_start[r];
-    for (int base = 0; base < T; base += blockDim.x) {
-      const int i = base + threadIdx.x;
-      const bool has = i < T && K[i] != kEmptyKey;
-      const unsigned m = __ballot_sync(0xffffffffu, has);
+#pragma unroll
+    for (int p = 0; p < kPasses; p++) {
+      if ((int64_t)p * THREADS >= len) break;
+      const bool c = (claimed >> p) & 1u;
+      const unsigned m = __ballot_sync(0xffffffffu, c);
       unsigned wpos = 0;
       if (lane == 0 && m) wpos = atomicAdd(&s_out, (unsigned)__popc(m));
       wpos = __shfl_sync(0xffffffffu, wpos, 0);
-      if (has) {
+      if (c) {
         const unsigned pos = wpos + __popc(m & lt);
-        adj_out[ob + pos] = K[i];
-        W_out[ob + pos] = (int64_t)V[i];
+        adj_out[ob + pos] = K[slot[p]];
+        W_out[ob + pos] = (int64_t)V[slot[p]];
+        K[slot[p]] = kEmptyKey;
+        V[slot[p]] = 0ull;
       }
     }
     __syncthreads();
@@ -682,7 +716,7 @@ void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const
   if (nrows <= 0) return;
   static bool attr_set = false;
   if (!attr_set) {
-    GP_CUDA(cudaFuncSetAttribute(k_merge_hash_blk<kHashTB3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GP_CUDA(cudaFuncSetAttribute(k_merge_hash_blk<kHashTB3, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kHashSmemB3));
     attr_set = true;
   }
@@ -713,10 +747,10 @@ void merge_rows_unordered(const TwoSrc& src, int64_t nrows, int64_t ncols, const
               (const int32_t*)nullptr, (const unsigned*)nullptr, out_start, deg_out, adj_out, W_out, l2, cnts,
               (int64_t)kHashT2 / 2, l3, cnts + 1, (int64_t)kBlockCap, lh, cnts + 2, family);
   }
-  GP_LAUNCH(family, k_merge_hash_blk<kHashTB2>, (unsigned)(8 * sms), 256, kHashSmemB2, s, src, (const int32_t*)l2,
-            (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, family);
-  GP_LAUNCH(family, k_merge_hash_blk<kHashTB3>, (unsigned)sms, 1024, kHashSmemB3, s, src, (const int32_t*)l3,
-            (const unsigned*)(cnts + 1), out_start, deg_out, adj_out, W_out, family);
+  GP_LAUNCH(family, (k_merge_hash_blk<kHashTB2, 256>), (unsigned)(8 * sms), 256, kHashSmemB2, s, src,
+            (const int32_t*)l2, (const unsigned*)cnts, out_start, deg_out, adj_out, W_out, family);
+  GP_LAUNCH(family, (k_merge_hash_blk<kHashTB3, 1024>), (unsigned)sms, 1024, kHashSmemB3, s, src,
+            (const int32_t*)l3, (const unsigned*)(cnts + 1), out_start, deg_out, adj_out, W_out, family);
   int nbits = 1;
   while (nbits < 31 && (int64_t(1) << nbits) < ncols) nbits++;
   int32_t* tk = dnew<int32_t>(raw_bound, s);
