@@ -467,6 +467,19 @@ def batch_spec(count: int = 4096, nmin: int = 100, nmax: int = 50000, base_seed:
     return spec
 
 
+def spec_edges(item) -> int:
+    """Directed edge count of a batch item's graph (the tiled graphs are built once per T, the
+    layered count is the recipe's)."""
+    kind, p, _ = item
+    if kind in ("cholesky", "lu"):
+        return int(_tiled(kind, p)["m"])
+    layers, width = p
+    cap = 0
+    for ls in range(layers - 1):
+        cap += width * width * min(4, layers - 1 - ls)
+    return min(8 * layers * width, cap)
+
+
 @functools.lru_cache(maxsize=None)
 def _tiled(kind: str, T: int):
     return cholesky(T) if kind == "cholesky" else lu(T)
