@@ -1,4 +1,5 @@
-// k_scan.cuh -- exclusive prefix sums (reduce-then-scan, three launches, no inter-block waits).
+// k_scan.cuh -- exclusive prefix sums (reduce-then-scan, three launches, no inter-block waits; inputs of
+// at most a few tiles: one block in one launch, the tiles in turn with a running carry).
 #pragma once
 #include "gp_internal.cuh"
 
@@ -94,6 +95,37 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const Tin* __restric
   }
 }
 
+// One block over every tile of a short input, in order, carrying the running total.
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(kScanThreads) k_scan_one_block(const Tin* __restrict__ in, int64_t n,
+                                                                 Tout* __restrict__ out) {
+  __shared__ Tout sh[33];
+  Tout carry = 0;
+  for (int64_t t0 = 0; t0 < n; t0 += kScanTile) {
+    const int64_t base = t0 + (int64_t)threadIdx.x * kScanItems;
+    Tout v[kScanItems];
+    Tout sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+      const int64_t idx = base + i;
+      v[i] = (idx < n) ? (Tout)in[idx] : Tout(0);
+      sum += v[i];
+    }
+    Tout tot;
+    Tout run = block_exclusive_scan<Tout>(sum, sh, &tot) + carry;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+      const int64_t idx = base + i;
+      if (idx < n) out[idx] = run;
+      run += v[i];
+      if (idx == n - 1) out[n] = run;
+    }
+    carry += tot;
+  }
+}
+
+constexpr int64_t kScanOneBlockTiles = 4;  // up to here one launch beats three
+
 template <class Tin, class Tout>
 static void scan_impl(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
   if (n <= 0) {
@@ -101,6 +133,11 @@ static void scan_impl(const Tin* in, Tout* out, int64_t n, cudaStream_t s) {
     return;
   }
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  if (nb <= kScanOneBlockTiles) {
+    GP_LAUNCH(F_SCAN, (k_scan_one_block<Tin, Tout>), 1, kScanThreads, 0, s, in, n, out);
+    GP_CHECK_LAUNCH();
+    return;
+  }
   Tout* partial = dnew<Tout>(nb, s);
   GP_LAUNCH(F_SCAN, (k_scan_reduce<Tin, Tout>), (unsigned)nb, kScanThreads, 0, s, in, n, partial);
   GP_LAUNCH(F_SCAN, (k_scan_partials<Tout>), 1, 1024, 0, s, partial, nb);
