@@ -508,10 +508,11 @@ def main():
 
     fixed = None
     if not big:
-        fixed = bench_fixed(g, K, W, stream, flush, with_oracle=not args.no_cpu_baseline)
+        fixed = bench_fixed(g, K, W, stream, flush, with_oracle=not args.no_cpu_baseline and world == 1)
     learned = None
     if not args.no_learned:
-        learned = bench_learned(g, dg, part, res, ms, K, W, stream, flush, bgen.held_out() if bgen else [])
+        learned = bench_learned(g, dg, part, res, ms, K, W, stream, flush, bgen.held_out() if bgen else [],
+                                with_oracle=not args.no_cpu_baseline and world == 1)
     batch = None
     if bgen is not None:
         batch = bench_batch(bgen.graphs(), K, W, stream, flush, with_cpu=not args.no_cpu_baseline)
@@ -565,7 +566,6 @@ def bench_fixed(g, K, W, stream, flush, with_oracle):
     that vertex, and (unless the CPU baseline is off) bit-exactness against the oracle."""
     import numpy as np
     import torch
-    import oracle
     import paper_1502_07451_b300 as gp
     from paper_1502_07451_b300 import gen
     hs, src = gen.with_host_source(g, 0)
@@ -609,19 +609,19 @@ def bench_fixed(g, K, W, stream, flush, with_oracle):
            "ms_per_step": total / K, "cut": res["cut"], "feasible": res["feasible"], "makespan_ns": mk,
            "host_vertex_on_cpu": bool(p[src] == 0),
            "without_pin": {"cut": rfree["cut"], "host_vertex_side": int(free_part[src].item())}}
-    if with_oracle:
+    if with_oracle:  # part of the CPU-baseline leg
+        import oracle
         opart, ores = oracle.partition(hs, fixed=fx)
         out["bit_exact_vs_oracle"] = bool(np.array_equal(opart, p) and ores["cut"] == res["cut"]
                                           and ores["load_cpu"] == res["load_cpu"])
     return out
 
 
-def bench_learned(g, dg, part_plain, res_plain, ms_plain, K, W, stream, flush, held_out):
+def bench_learned(g, dg, part_plain, res_plain, ms_plain, K, W, stream, flush, held_out, with_oracle=True):
     """The learned path (network proposal + refinement of level 0) on the same workload, with the
     trained checkpoint; plus the cut against the plain path on held-out 1M-vertex layered DAGs."""
     import torch
     import paper_1502_07451_b300 as gp
-    import oracle
     if not os.path.exists(MODEL_PATH):
         return {"unavailable": "no trained checkpoint at paper_1502_07451_b300/models/mpnn3_h64.bin"}
     keys = ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")
@@ -663,9 +663,12 @@ def bench_learned(g, dg, part_plain, res_plain, ms_plain, K, W, stream, flush, h
     fams = gp.kernel_families()
     mp = gp.gp_prof_read(fams.index("mpnn"))
     gp.gp_prof_reset()
-    # the integer result from these logits, recomputed by the oracle
-    opart, ores = oracle.partition_learned(g, logits.cpu().numpy())
-    exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == r["cut"])
+    # the integer result from these logits, recomputed by the oracle (with the CPU baseline leg only)
+    exact = None
+    if with_oracle:
+        import oracle
+        opart, ores = oracle.partition_learned(g, logits.cpu().numpy())
+        exact = bool(np.array_equal(opart, part.cpu().numpy()) and ores["cut"] == r["cut"])
     held = []
     for seed, hg in zip(HELD_OUT_SEEDS, held_out):
         dh = {k: torch.from_numpy(hg[k]).cuda() for k in keys}
@@ -937,7 +940,6 @@ def run_cholesky_line(args, rank, world, local_rank):
     plain path batched and one graph after another."""
     import torch
     import paper_1502_07451_b300 as gp
-    import oracle
     from paper_1502_07451_b300 import gen
     torch.cuda.set_device(local_rank)
     gp.lib()
@@ -1019,7 +1021,8 @@ def run_cholesky_line(args, rank, world, local_rank):
     e2e_s = time.perf_counter() - t0
     e2e_ok = all(torch.equal(a.cpu(), b) for a, b in zip(parts, hparts))
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline:  # the CPU-baseline leg
+        import oracle
         t0 = time.perf_counter()
         opart, ores = oracle.partition(g, seed=0)
         oracle.makespan(g, opart)
