@@ -29,7 +29,7 @@ namespace gp {
 
 const char* const kFamilyName[F_COUNT] = {
     "validate", "transpose", "levels", "sym_merge", "match_pick", "match_confirm", "twohop", "cmap",
-    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch", "mpnn", "propose"};
+    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch", "mpnn", "propose", "refine"};
 
 // ------------------------------------------------------------------------------------------------
 // launch accounting and optional per-launch event timing
@@ -843,6 +843,8 @@ struct TraceDev {
   int32_t trial;
   int32_t bad;
   Ctl ctl;
+  unsigned grid_bar;  // arrivals at the grid refinement's barrier
+  int32_t tail_err;   // a grid refinement barrier wait expired
 };
 
 static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
@@ -977,7 +979,8 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
     cand.dirty[1] = A.get<int32_t>(n);
     GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
     // the coarse levels (at most kTailMaxVertices vertices each) in one CTA launch, the next ones (up to
-    // kClusterTailMaxVertices) in one cluster launch, then the rest level by level over the whole grid
+    // kClusterTailMaxVertices) in one cluster launch, then the rest in one cooperative grid launch (level
+    // by level, a launch per step, where the device has no cooperative launch)
     auto tail_args = [&](int a, int b, double gscale) {  // levels b (coarser) down to a
       TailArgs ta;
       memset(&ta, 0, sizeof(ta));
@@ -999,18 +1002,50 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
     while (lo - 1 >= 0 && L[lo - 1].n <= kTailMaxVertices && Lc - (lo - 1) + 1 <= kTailMaxLevels) lo--;
     if (lo <= Lc) {
       const TailArgs ta = tail_args(lo, Lc, 1.0);
-      GP_LAUNCH(F_SELECT, k_refine_tail<false>, 1, 1024, 0, s, ta, &td->ctl, cand, td->rounds, td->moves, td->bal,
-                td->balmoves);
+      GP_LAUNCH(F_REFINE, k_refine_tail<kTailCta>, 1, 1024, 0, s, ta, &td->ctl, cand, td->rounds, td->moves,
+                td->bal, td->balmoves, (unsigned*)nullptr, (int*)nullptr);
     }
     {
       int lo2 = lo;
       while (lo2 - 1 >= 0 && L[lo2 - 1].n <= kClusterTailMaxVertices && lo - (lo2 - 1) <= kTailMaxLevels) lo2--;
-      const int cs = lo2 < lo ? cluster_max((const void*)k_refine_tail<true>, 1024, 0) : 0;
+      const int cs = lo2 < lo ? cluster_max((const void*)k_refine_tail<kTailCluster>, 1024, 0) : 0;
       if (lo2 < lo && cs > 0) {
         const TailArgs ta = tail_args(lo2, lo - 1, 0.25);
-        GP_CUDA(launch_cluster(F_SELECT, k_refine_tail<true>, cs, 1024, 0, s, ta, &td->ctl, cand, td->rounds,
-                               td->moves, td->bal, td->balmoves));
+        GP_CUDA(launch_cluster(F_REFINE, k_refine_tail<kTailCluster>, cs, 1024, 0, s, ta, &td->ctl, cand, td->rounds,
+                               td->moves, td->bal, td->balmoves, (unsigned*)nullptr, (int*)nullptr));
         lo = lo2;
+      }
+    }
+    if (lo > 0 && lo - 1 + 1 <= kTailMaxLevels) {
+      static int grid_blocks = -1;  // resident CTAs of the grid refinement (0: no cooperative launch)
+      if (grid_blocks < 0) {
+        int coop = 0, dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_tail<kTailGrid>, 1024, 0) ==
+                        cudaSuccess)
+          grid_blocks = per_sm > 0 ? num_sms() * per_sm : 0;
+        else
+          grid_blocks = 0;
+        cudaGetLastError();
+      }
+      if (grid_blocks > 0) {
+        TailArgs ta = tail_args(0, lo - 1, 0.25);
+        Ctl* ctl_p = &td->ctl;
+        int32_t* a_rounds = td->rounds;
+        long long* a_moves = td->moves;
+        int32_t* a_bal = td->bal;
+        long long* a_balmoves = td->balmoves;
+        unsigned* a_bar = &td->grid_bar;
+        int* a_err = &td->tail_err;
+        void* args[] = {(void*)&ta, (void*)&ctl_p, (void*)&cand, (void*)&a_rounds, (void*)&a_moves,
+                        (void*)&a_bal, (void*)&a_balmoves, (void*)&a_bar, (void*)&a_err};
+        launch_begin(F_REFINE, s);
+        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_refine_tail<kTailGrid>, dim3(grid_blocks),
+                                                          dim3(1024), args, 0, s);
+        launch_end(F_REFINE, s);
+        GP_CUDA(e);
+        lo = 0;
       }
     }
     for (int l = lo - 1; l >= 0; l--) {
@@ -1029,6 +1064,7 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
     TraceDev h;
     GP_CUDA(cudaMemcpyAsync(&h, td, sizeof(TraceDev), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
+    if (h.tail_err) throw Fail{GP_ERR_TIMEOUT};
     R.cut = (int64_t)h.cut;
     R.load_cpu = h.ctl.LC;
     R.load_gpu = h.ctl.LG;

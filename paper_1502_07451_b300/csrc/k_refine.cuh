@@ -16,6 +16,7 @@
 #pragma once
 #include "gp_internal.cuh"
 #include "k_coarsen.cuh"
+#include "k_makespan.cuh"  // grid_wait_bounded
 
 namespace gp {
 
@@ -119,7 +120,7 @@ __global__ void k_ref_begin(Ctl* ctl, int idbits) { ref_begin(ctl, idbits); }
 // gain of every vertex (a group of G lanes per row), once per level
 template <int G>
 __device__ void gain_all(const LevelGraph& g, const uint8_t* __restrict__ part, long long* __restrict__ gainv,
-                         int64_t tid, int64_t stride) {
+                         int64_t tid, int64_t stride, int fam = F_GAIN) {
   __shared__ unsigned long long sacc[32];
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
@@ -151,7 +152,7 @@ __device__ void gain_all(const LevelGraph& g, const uint8_t* __restrict__ part, 
     for (int o = G / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(gmask, acc, o, G);
     if (v < g.n && sub == 0) gainv[v] = acc;
   }
-  account(F_GAIN, bytes, sacc);
+  account(fam, bytes, sacc);
 }
 template <int G>
 __global__ void __launch_bounds__(256)
@@ -177,7 +178,7 @@ __device__ __forceinline__ void push_cand(CandCounters* cc, const Cands& cand, i
 // round's moves made stale (stamp == prev_tag), whose gains are recomputed here by a warp each and
 // stored back.  Both parts write disjoint vertices.
 __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag,
-                          const Cands& cand, int64_t tid, int64_t stride) {
+                          const Cands& cand, int64_t tid, int64_t stride, int fam = F_GAIN) {
   __shared__ long long sh[32];
   __shared__ unsigned long long shu[32];
   __shared__ unsigned long long sacc[32];
@@ -283,7 +284,7 @@ __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part,
       if (sum_cs) atomicAdd(&cc->cost_src, sum_cs);
     }
   }
-  account(F_GAIN, bytes, sacc);
+  account(fam, bytes, sacc);
 }
 __global__ void __launch_bounds__(256)
     k_ref_cands(LevelGraph g, const uint8_t* __restrict__ part, Ctl* ctl, int r, int32_t prev_tag, Cands cand) {
@@ -452,7 +453,7 @@ __global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, Cands cand
 // Moves the accepted candidates and stamps them and their neighbours as stale for the next round
 // (a warp per candidate; atomicExch on the stamp lists each stale vertex once).
 __device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restrict__ part, int32_t tag,
-                          const Cands& cand, int64_t tid, int64_t stride) {
+                          const Cands& cand, int64_t tid, int64_t stride, int fam = F_APPLY) {
   __shared__ long long sh[32];
   __shared__ unsigned long long sacc[32];
   __shared__ int s_go;
@@ -523,7 +524,7 @@ __device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restr
     if (dC) atomicAdd((unsigned long long*)&ctl->LC, (unsigned long long)dC);
     if (dG) atomicAdd((unsigned long long*)&ctl->LG, (unsigned long long)dG);
   }
-  account(F_APPLY, bytes, sacc);
+  account(fam, bytes, sacc);
 }
 __global__ void __launch_bounds__(256)
     k_ref_apply(Ctl* ctl, int r, LevelGraph g, uint8_t* __restrict__ part, int32_t tag, Cands cand) {
@@ -593,24 +594,51 @@ struct TailArgs {
   TailLevel lev[kTailMaxLevels];  // lev[l - lo]
 };
 
-// CLUSTER: the same over one thread-block cluster (the cluster's threads share each step, the cluster
-// barrier separates the steps, the one-block selection runs in rank 0), for levels a little larger.
-template <bool CLUSTER>
+// MODE kTailCluster: the same over one thread-block cluster (the cluster's threads share each step, the
+// cluster barrier separates the steps, the one-block selection runs in rank 0), for levels a little
+// larger.  MODE kTailGrid: the same over a cooperative grid (one CTA per SM at most, all resident), for
+// the large levels: a grid barrier of its own separates the steps (a counter that every CTA increments
+// and polls, the wait bounded by the global timer at 0.5 s; on expiry the CTA stops, sets *err, and the
+// other CTAs' waits then expire too), replacing ~31 launches per level.
+constexpr int kTailCta = 0, kTailCluster = 1, kTailGrid = 2;
+
+__device__ __forceinline__ bool tail_grid_sync(unsigned* bar, unsigned& epoch, int* err) {
+  __syncthreads();
+  bool ok = true;
+  epoch += 1;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's writes before its arrival
+    atomicAdd(bar, 1u);
+    ok = grid_wait_bounded(bar, epoch * gridDim.x);
+    if (!ok) atomicOr(err, 1);
+    __threadfence();
+  }
+  return __syncthreads_or(!ok) == 0;
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(1024, 1)
     k_refine_tail(TailArgs A, Ctl* ctl, Cands cand, int32_t* t_rounds, long long* t_moves, int32_t* t_bal,
-                  long long* t_balmoves) {
+                  long long* t_balmoves, unsigned* bar, int* err) {
   uint32_t rank = 0, nranks = 1;
-  if (CLUSTER) {
+  if (MODE == kTailCluster) {
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nranks));
+  } else if (MODE == kTailGrid) {
+    rank = blockIdx.x;
+    nranks = gridDim.x;
   }
   const int64_t tid = (int64_t)rank * blockDim.x + threadIdx.x, stride = (int64_t)nranks * blockDim.x;
   const bool lead = rank == 0 && threadIdx.x == 0;
-  auto sync = [&]() {
-    if (CLUSTER)
+  unsigned epoch = 0;
+  auto sync = [&]() -> bool {
+    if (MODE == kTailCluster) {
       cluster_sync();
-    else
-      __syncthreads();
+      return true;
+    }
+    if (MODE == kTailGrid) return tail_grid_sync(bar, epoch, err);
+    __syncthreads();
+    return true;
   };
   for (int l = A.hi; l >= A.lo; l--) {
     const TailLevel& T = A.lev[l - A.lo];
@@ -619,23 +647,23 @@ __global__ void __launch_bounds__(1024, 1)
     if (pc)
       for (int64_t v = tid; v < g.n; v += stride) T.part[v] = pc[T.cmap[v]];
     if (lead) ref_begin(ctl, T.idbits);
-    sync();
+    if (!sync()) return;
     switch (T.G) {
-      case 2: gain_all<2>(g, T.part, cand.gainv, tid, stride); break;
-      case 4: gain_all<4>(g, T.part, cand.gainv, tid, stride); break;
-      case 8: gain_all<8>(g, T.part, cand.gainv, tid, stride); break;
-      case 16: gain_all<16>(g, T.part, cand.gainv, tid, stride); break;
-      default: gain_all<32>(g, T.part, cand.gainv, tid, stride); break;
+      case 2: gain_all<2>(g, T.part, cand.gainv, tid, stride, F_REFINE); break;
+      case 4: gain_all<4>(g, T.part, cand.gainv, tid, stride, F_REFINE); break;
+      case 8: gain_all<8>(g, T.part, cand.gainv, tid, stride, F_REFINE); break;
+      case 16: gain_all<16>(g, T.part, cand.gainv, tid, stride, F_REFINE); break;
+      default: gain_all<32>(g, T.part, cand.gainv, tid, stride, F_REFINE); break;
     }
-    sync();
+    if (!sync()) return;
     int32_t prev = round_tag(l, -2);
     for (int r = -1; r < kRefineRounds; r++) {
-      ref_cands(g, T.part, ctl, r, prev, cand, tid, stride);
-      sync();
+      ref_cands(g, T.part, ctl, r, prev, cand, tid, stride, F_REFINE);
+      if (!sync()) return;
       if (rank == 0) ref_select(ctl, r, cand);
-      sync();
-      ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, tid, stride);
-      sync();
+      if (!sync()) return;
+      ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, tid, stride, F_REFINE);
+      if (!sync()) return;
       prev = round_tag(l, r);
       if (*(volatile int32_t*)&ctl->done) break;  // later rounds would return at once (uniform: read after the barrier)
     }
@@ -645,7 +673,7 @@ __global__ void __launch_bounds__(1024, 1)
       t_bal[l] = ctl->balanced;
       t_balmoves[l] = ctl->bal_moves;
     }
-    sync();
+    if (!sync()) return;
   }
 }
 
