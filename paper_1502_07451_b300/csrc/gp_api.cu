@@ -1030,6 +1030,9 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
         cudaGetLastError();
       }
       if (grid_blocks > 0) {
+        // every CTA must be resident at once: a deferred creation's level traversal, which may still hold
+        // SMs on its side stream for a long chain of levels, finishes first (long done in the usual case)
+        if (g->lev_event) GP_CUDA(cudaStreamWaitEvent(s, g->lev_event, 0));
         TailArgs ta = tail_args(0, lo - 1, 0.25);
         Ctl* ctl_p = &td->ctl;
         int32_t* a_rounds = td->rounds;
@@ -1044,8 +1047,12 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
         const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_refine_tail<kTailGrid>, dim3(grid_blocks),
                                                           dim3(1024), args, 0, s);
         launch_end(F_REFINE, s);
-        GP_CUDA(e);
-        lo = 0;
+        if (e == cudaSuccess) {
+          lo = 0;
+        } else {  // no room for the whole grid (e.g. a shared or partitioned device): a launch per step
+          cudaGetLastError();
+          grid_blocks = 0;
+        }
       }
     }
     for (int l = lo - 1; l >= 0; l--) {
