@@ -386,6 +386,12 @@ GP_API gp_status gp_batch_partition_learned(int32_t count, gp_graph* const* grap
  * limit outside the range. */
 GP_API gp_status gp_selftest_wait_timeout(int32_t limit_ms, void* stream);
 
+/* Failure-path self-check of the grid barrier that the wide-level makespan and the large-level
+ * refinement use (no fault involved): a cooperative launch of two CTAs in which CTA 1 returns without
+ * arriving, so CTA 0's bounded wait (0.5 s) gives up.  Returns GP_ERR_TIMEOUT when it did (the context
+ * stays usable), GP_ERR_CUDA if the device has no cooperative launch. */
+GP_API gp_status gp_selftest_grid_wait_timeout(void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation.
  * gp_launch_count: kernels launched by this library since load (all threads).

@@ -114,6 +114,7 @@ def lib():
                 "gp_batch_partition_learned": [_I32, _P, _P, _P, _D, _P, _P, _P, _P],
                 "gp_graph_create_batch": [_I32, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P],
                 "gp_selftest_wait_timeout": [_I32, _P],
+                "gp_selftest_grid_wait_timeout": [_P],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)

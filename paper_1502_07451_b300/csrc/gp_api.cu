@@ -1112,6 +1112,30 @@ gp_status gp_partition_fixed(gp_graph* g, const int8_t* fixed, double r_cpu, dou
   return partition_impl(g, fixed, r_cpu, tol, seed, part_out, res, stream);
 }
 
+gp_status gp_selftest_grid_wait_timeout(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    unsigned* bar = A.get<unsigned>(1);
+    int* err = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+    GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+    void* args[] = {(void*)&bar, (void*)&err};
+    launch_begin(F_MISC, s);
+    const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_grid_wait_selftest, dim3(2), dim3(32), args, 0, s);
+    launch_end(F_MISC, s);
+    GP_CUDA(e);
+    int herr = 0;
+    GP_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    return herr ? GP_ERR_TIMEOUT : GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
 gp_status gp_last_trace(const gp_graph* g, gp_trace* trace) {
   if (!g || !trace) return GP_ERR_INVALID;
   *trace = g->trace;

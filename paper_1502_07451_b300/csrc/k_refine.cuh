@@ -616,6 +616,14 @@ __device__ __forceinline__ bool tail_grid_sync(unsigned* bar, unsigned& epoch, i
   return __syncthreads_or(!ok) == 0;
 }
 
+// Failure-path self-check of the grid barrier: CTA 1 returns without arriving, so CTA 0's wait runs out
+// (0.5 s), sets *err and returns.
+__global__ void k_grid_wait_selftest(unsigned* bar, int* err) {
+  if (blockIdx.x != 0) return;
+  unsigned epoch = 0;
+  tail_grid_sync(bar, epoch, err);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(1024, 1)
     k_refine_tail(TailArgs A, Ctl* ctl, Cands cand, int32_t* t_rounds, long long* t_moves, int32_t* t_bal,

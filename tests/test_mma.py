@@ -38,6 +38,26 @@ def test_mma_rejects_bad_shapes():
         gp.gp_step_mma_bf16(A.cpu(), B.cpu(), C.cpu())
 
 
+def test_grid_barrier_wait_gives_up_and_the_context_stays_usable():
+    """The grid barrier of the wide-level makespan and the large-level refinement: with one CTA that
+    never arrives, the other's bounded wait gives up (GP_ERR_TIMEOUT), and a partition that uses the
+    barrier then runs normally."""
+    import time
+    import oracle
+    from paper_1502_07451_b300 import gen
+    L = gp.lib()
+    t0 = time.perf_counter()
+    assert L.gp_selftest_grid_wait_timeout(None) == gp.GP_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    g = gen.layered(40, 600, 90000, 3)  # levels above 16,384 vertices: the grid refinement runs
+    dg = {k: torch.from_numpy(g[k]).cuda() for k in ("offsets", "cols", "edge_cost", "cpu_cost", "gpu_cost")}
+    with gp.Graph(dict(dg, n=g["n"], m=g["m"])) as G:
+        part = torch.empty(g["n"], dtype=torch.uint8, device="cuda")
+        res = G.partition(part)
+    opart, ores = oracle.partition(g)
+    assert np.array_equal(part.cpu().numpy(), opart) and res["cut"] == ores["cut"]
+
+
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
     """A device wait on an mbarrier that nothing arrives at gives up after its limit and reports
     GP_ERR_TIMEOUT; tensor memory is released and the next product runs normally."""
