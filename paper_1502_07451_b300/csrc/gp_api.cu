@@ -1016,45 +1016,10 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
         lo = lo2;
       }
     }
-    if (lo > 0 && lo - 1 + 1 <= kTailMaxLevels) {
-      static int grid_blocks = -1;  // resident CTAs of the grid refinement (0: no cooperative launch)
-      if (grid_blocks < 0) {
-        int coop = 0, dev = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_tail<kTailGrid>, 1024, 0) ==
-                        cudaSuccess)
-          grid_blocks = per_sm > 0 ? num_sms() * per_sm : 0;
-        else
-          grid_blocks = 0;
-        cudaGetLastError();
-      }
-      if (grid_blocks > 0) {
-        // every CTA must be resident at once: a deferred creation's level traversal, which may still hold
-        // SMs on its side stream for a long chain of levels, finishes first (long done in the usual case)
-        if (g->lev_event) GP_CUDA(cudaStreamWaitEvent(s, g->lev_event, 0));
-        TailArgs ta = tail_args(0, lo - 1, 0.25);
-        Ctl* ctl_p = &td->ctl;
-        int32_t* a_rounds = td->rounds;
-        long long* a_moves = td->moves;
-        int32_t* a_bal = td->bal;
-        long long* a_balmoves = td->balmoves;
-        unsigned* a_bar = &td->grid_bar;
-        int* a_err = &td->tail_err;
-        void* args[] = {(void*)&ta, (void*)&ctl_p, (void*)&cand, (void*)&a_rounds, (void*)&a_moves,
-                        (void*)&a_bal, (void*)&a_balmoves, (void*)&a_bar, (void*)&a_err};
-        launch_begin(F_REFINE, s);
-        const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_refine_tail<kTailGrid>, dim3(grid_blocks),
-                                                          dim3(1024), args, 0, s);
-        launch_end(F_REFINE, s);
-        if (e == cudaSuccess) {
-          lo = 0;
-        } else {  // no room for the whole grid (e.g. a shared or partitioned device): a launch per step
-          cudaGetLastError();
-          grid_blocks = 0;
-        }
-      }
-    }
+    if (lo > 0 && lo <= kTailMaxLevels &&
+        launch_refine_grid(tail_args(0, lo - 1, 0.25), &td->ctl, cand, td->rounds, td->moves, td->bal, td->balmoves,
+                           &td->grid_bar, &td->tail_err, g->lev_event, s))
+      lo = 0;
     for (int l = lo - 1; l >= 0; l--) {
       if (l < Lc) {  // the coarsest level holds the growing's split
         parts[l] = A.get<uint8_t>(L[l].n);

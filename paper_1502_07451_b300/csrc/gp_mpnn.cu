@@ -609,7 +609,25 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
     cand.dirty[1] = A.get<int32_t>(n);
     GP_CUDA(cudaMemsetAsync(cand.stamp, 0xff, sizeof(int32_t) * n, s));
     refine_loads(g->L0, part, ctl, s);
-    refine_level_run(g->L0, part, ctl, cand, 0, (double)g->a0 / (double)n, s);
+    // one cooperative grid launch for the level (a launch per step where the grid does not fit)
+    int* terr = A.get<int>(1);
+    GP_CUDA(cudaMemsetAsync(terr, 0, sizeof(int), s));
+    {
+      TailArgs ta;
+      memset(&ta, 0, sizeof(ta));
+      ta.lev[0].g = g->L0;
+      ta.lev[0].part = part;
+      ta.lev[0].G = group_for_degree(0.25 * (double)g->a0 / (double)n);
+      ta.lev[0].idbits = idbits_for(n);
+      int32_t* t_rounds = A.get<int32_t>(1);
+      int32_t* t_bal = A.get<int32_t>(1);
+      long long* t_moves = A.get<long long>(1);
+      long long* t_balmoves = A.get<long long>(1);
+      unsigned* bar = A.get<unsigned>(1);
+      GP_CUDA(cudaMemsetAsync(bar, 0, sizeof(unsigned), s));
+      if (!launch_refine_grid(ta, ctl, cand, t_rounds, t_moves, t_bal, t_balmoves, bar, terr, g->lev_event, s))
+        refine_level_run(g->L0, part, ctl, cand, 0, (double)g->a0 / (double)n, s);
+    }
     unsigned long long* cut = A.get<unsigned long long>(1);
     int* bad = A.get<int>(1);
     GP_CUDA(cudaMemsetAsync(cut, 0, sizeof(unsigned long long), s));
@@ -619,9 +637,12 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
     GP_CUDA(cudaMemcpyAsync(part_out, part, (size_t)n, cudaMemcpyDefault, s));
     if (prof) cudaEventRecord(ev[3], s);
     unsigned long long hcut = 0;
+    int hterr = 0;
     GP_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaMemcpyAsync(&hcut, cut, sizeof(hcut), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaMemcpyAsync(&hterr, terr, sizeof(int), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
+    if (hterr) return GP_ERR_TIMEOUT;
     R.cut = (int64_t)hcut;
     R.load_cpu = hc.LC;
     R.load_gpu = hc.LG;

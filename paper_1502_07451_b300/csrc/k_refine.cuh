@@ -710,4 +710,42 @@ void refine_level_run(const LevelGraph& g, uint8_t* part, Ctl* ctl, const Cands&
   GP_CHECK_LAUNCH();
 }
 
+// The levels of `ta` in one cooperative grid launch of k_refine_tail<kTailGrid> (one CTA of 1,024 threads per
+// SM, all resident).  *bar and *err must be zero.  `wait_for` (nullable): work that may still hold SMs on
+// another stream (a deferred creation's level traversal), waited for first.  Returns false, having
+// launched nothing, where the device cannot hold the whole grid; the caller then runs a launch per step.
+static bool launch_refine_grid(const TailArgs& ta, Ctl* ctl, const Cands& cand, int32_t* t_rounds,
+                               long long* t_moves, int32_t* t_bal, long long* t_balmoves, unsigned* bar, int* err,
+                               cudaEvent_t wait_for, cudaStream_t s) {
+  static int grid_blocks = -1;  // resident CTAs of the grid (0: no cooperative launch)
+  if (grid_blocks < 0) {
+    int coop = 0, dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (coop && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_refine_tail<kTailGrid>, 1024, 0) ==
+                    cudaSuccess)
+      grid_blocks = per_sm > 0 ? num_sms() * per_sm : 0;
+    else
+      grid_blocks = 0;
+    cudaGetLastError();
+  }
+  if (grid_blocks <= 0) return false;
+  if (wait_for) GP_CUDA(cudaStreamWaitEvent(s, wait_for, 0));
+  TailArgs a = ta;
+  Ctl* c = ctl;
+  Cands cd = cand;
+  void* args[] = {(void*)&a, (void*)&c, (void*)&cd, (void*)&t_rounds, (void*)&t_moves,
+                  (void*)&t_bal, (void*)&t_balmoves, (void*)&bar, (void*)&err};
+  launch_begin(F_REFINE, s);
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_refine_tail<kTailGrid>, dim3(grid_blocks),
+                                                    dim3(1024), args, 0, s);
+  launch_end(F_REFINE, s);
+  if (e != cudaSuccess) {  // no room for the whole grid (e.g. a shared or partitioned device)
+    cudaGetLastError();
+    grid_blocks = 0;
+    return false;
+  }
+  return true;
+}
+
 }  // namespace gp
