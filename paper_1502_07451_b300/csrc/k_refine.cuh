@@ -40,6 +40,7 @@ struct Ctl {
   int32_t done, streak, rounds, balanced, bal_active, pad;
   long long moves, bal_moves, take;
   unsigned long long ndirty[2];  // vertices whose gain a round's moves changed, double-buffered
+  long long sLC, sLG;            // the loads at the start of a round (the grid refinement's local selection)
 };
 
 struct Cands {
@@ -450,29 +451,46 @@ __device__ void ref_select(Ctl* ctl, int r, const Cands& cand) {  // one block
 }
 __global__ void __launch_bounds__(1024) k_ref_select(Ctl* ctl, int r, Cands cand) { ref_select(ctl, r, cand); }
 
-// Moves the accepted candidates and stamps them and their neighbours as stale for the next round
-// (a warp per candidate; atomicExch on the stamp lists each stale vertex once).
+// A round's selection as the moves need it.
+struct SelParams {
+  int go, accept, src, idbits;
+  unsigned long long N, hi, lo;
+  long long gmax;
+};
+
+__device__ void ref_apply_body(const SelParams sp, Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restrict__ part,
+                               int32_t tag, const Cands& cand, int64_t tid, int64_t stride, int fam);
+
 __device__ void ref_apply(Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restrict__ part, int32_t tag,
                           const Cands& cand, int64_t tid, int64_t stride, int fam = F_APPLY) {
-  __shared__ long long sh[32];
-  __shared__ unsigned long long sacc[32];
-  __shared__ int s_go;
-  __shared__ int s_accept, s_src, s_idbits;
-  __shared__ unsigned long long s_N, s_hi, s_lo;
-  __shared__ long long s_gmax;
+  __shared__ SelParams s_sp;
   if (threadIdx.x == 0) {
     const Ctl& c = *ctl;
-    s_go = (c.sel_round == r) && c.accept != 0;
-    s_accept = c.accept;
-    s_src = (r < 0) ? c.side_src : (r & 1);
-    s_idbits = c.idbits;
-    s_N = c.cc[(r < 0) ? 1 : (r & 1)].ncand;
-    s_hi = c.thr_hi;
-    s_lo = c.thr_lo;
-    s_gmax = c.sel_gmax;
+    s_sp.go = (c.sel_round == r) && c.accept != 0;
+    s_sp.accept = c.accept;
+    s_sp.src = (r < 0) ? c.side_src : (r & 1);
+    s_sp.idbits = c.idbits;
+    s_sp.N = c.cc[(r < 0) ? 1 : (r & 1)].ncand;
+    s_sp.hi = c.thr_hi;
+    s_sp.lo = c.thr_lo;
+    s_sp.gmax = c.sel_gmax;
   }
   __syncthreads();
-  if (!s_go) return;
+  const SelParams sp = s_sp;
+  ref_apply_body(sp, ctl, r, g, part, tag, cand, tid, stride, fam);
+}
+
+// Moves the accepted candidates and stamps them and their neighbours as stale for the next round
+// (a warp per candidate; atomicExch on the stamp lists each stale vertex once).  sp is the same in
+// every thread.
+__device__ void ref_apply_body(const SelParams sp, Ctl* ctl, int r, const LevelGraph& g, uint8_t* __restrict__ part,
+                               int32_t tag, const Cands& cand, int64_t tid, int64_t stride, int fam) {
+  __shared__ long long sh[32];
+  __shared__ unsigned long long sacc[32];
+  if (!sp.go) return;
+  const int s_accept = sp.accept, s_src = sp.src, s_idbits = sp.idbits;
+  const unsigned long long s_N = sp.N, s_hi = sp.hi, s_lo = sp.lo;
+  const long long s_gmax = sp.gmax;
   const int dst = 1 - s_src;
   const u128 thr = ((u128)s_hi << 64) | (u128)s_lo;
   const int lane = threadIdx.x & 31;
@@ -666,11 +684,63 @@ __global__ void __launch_bounds__(1024, 1)
     if (!sync()) return;
     int32_t prev = round_tag(l, -2);
     for (int r = -1; r < kRefineRounds; r++) {
+      if (MODE == kTailGrid && r >= 0 && lead) {
+        // ahead of the selection (which may then run in every CTA): the next round's counters and stale
+        // list (last used by the previous round), and the loads the selection compares against
+        reset_counters(ctl->cc[(r & 1) ^ 1]);
+        ctl->ndirty[(r + 1) & 1] = 0;
+        ctl->sLC = ctl->LC;
+        ctl->sLG = ctl->LG;
+      }
       ref_cands(g, T.part, ctl, r, prev, cand, tid, stride, F_REFINE);
       if (!sync()) return;
-      if (rank == 0) ref_select(ctl, r, cand);
-      if (!sync()) return;
-      ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, tid, stride, F_REFINE);
+      // a gain round whose selection takes all candidates or none needs no histogram: every CTA decides
+      // it from the round's counters (unchanged until the next barrier), CTA 0 records it, and the moves
+      // follow without the barrier a selection in one CTA needs
+      bool local = false;
+      SelParams sp{};
+      if (MODE == kTailGrid && r >= 0) {
+        const CandCounters* cc = &ctl->cc[r & 1];
+        const unsigned long long N = __ldcg(&cc->ncand);
+        const long long cost_dst = (long long)__ldcg(&cc->cost_dst);
+        const int dst = 1 - (r & 1);
+        const long long Ld = __ldcg(dst == 0 ? &ctl->sLC : &ctl->sLG);
+        const long long Bd = dst == 0 ? ctl->BC : ctl->BG;
+        long long k = -1;
+        if (N == 0 || Ld > Bd)
+          k = 0;
+        else if (cost_dst <= Bd - Ld)
+          k = (long long)N;
+        if (k >= 0) {
+          local = true;
+          sp.go = k > 0;
+          sp.accept = k > 0 ? 1 : 0;
+          sp.src = r & 1;
+          sp.idbits = ctl->idbits;
+          sp.N = N;
+          sp.gmax = __ldcg(&cc->gmax);
+          if (lead) {  // what the one-CTA selection records for the same round
+            Ctl& c = *ctl;
+            c.sel_round = r;
+            c.accept = sp.accept;
+            c.thr_hi = 0;
+            c.thr_lo = 0;
+            c.sel_gmax = sp.gmax;
+            c.take = k;
+            c.rounds += 1;
+            c.moves += k;
+            c.streak = (k == 0) ? c.streak + 1 : 0;
+            if (c.streak == 2) c.done = 1;
+          }
+        }
+      }
+      if (local) {
+        ref_apply_body(sp, ctl, r, g, T.part, round_tag(l, r), cand, tid, stride, F_REFINE);
+      } else {
+        if (rank == 0) ref_select(ctl, r, cand);
+        if (!sync()) return;
+        ref_apply(ctl, r, g, T.part, round_tag(l, r), cand, tid, stride, F_REFINE);
+      }
       if (!sync()) return;
       prev = round_tag(l, r);
       if (*(volatile int32_t*)&ctl->done) break;  // later rounds would return at once (uniform: read after the barrier)
