@@ -619,9 +619,11 @@ static inline int group_for_avg(double avg) {
   if (avg <= 24.0) return 16;
   return 32;
 }
-// matching rounds: about eight row entries per lane (fewer lanes per vertex: less key-reduction work
-// per vertex; measured on the 1M workload, 12.05 -> 11.35 ms per partition against two per lane)
-static inline int group_for_match(double avg) { return group_for_avg(avg * 0.125); }
+// matching rounds: about sixteen row entries per lane (fewer lanes per vertex: less key-reduction work
+// per vertex; measured on the 1M workload, 12.05 -> 11.35 ms per partition with eight against two per
+// lane, then picks 2.28 -> 2.18 ms per step with sixteen against eight, and 29.8 -> 28.8 ms on the 16M
+// workload; four and thirty-two measured slower)
+static inline int group_for_match(double avg) { return group_for_avg(avg * 0.0625); }
 
 void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, int rounds, bool twohop,
                  int32_t* mate, cudaStream_t s) {
