@@ -1016,8 +1016,11 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
         lo = lo2;
       }
     }
+    // the grid's gain passes with about eight row entries per lane (its CTAs hold half the threads a
+    // launch per step did; refine 2.90 -> 2.87 ms per step on the 1M workload, 20.0 -> 19.4 ms on the 16M
+    // one, against about four; sixteen was slower)
     if (lo > 0 && lo <= kTailMaxLevels &&
-        launch_refine_grid(tail_args(0, lo - 1, 0.25), &td->ctl, cand, td->rounds, td->moves, td->bal, td->balmoves,
+        launch_refine_grid(tail_args(0, lo - 1, 0.125), &td->ctl, cand, td->rounds, td->moves, td->bal, td->balmoves,
                            &td->grid_bar, &td->tail_err, g->lev_event, s))
       lo = 0;
     for (int l = lo - 1; l >= 0; l--) {
