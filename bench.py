@@ -162,6 +162,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi's start-up (driver queries) stays out of the timed region: wait for its first sample
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
@@ -252,11 +256,12 @@ def run_reference_batch(args, rank, world):
 
 
 def quiet_heap():
-    """Collect the heap once and freeze it, so that no garbage-collection pass over the (large) input
-    graphs lands in a timed region."""
+    """Collect the heap once, freeze it and switch the collector off, so that no garbage-collection pass
+    over the (large) input graphs lands in a timed region."""
     import gc
     gc.collect()
     gc.freeze()
+    gc.disable()  # and no pass at all until the line is printed (the bench allocates little meanwhile)
 
 
 def max_over_ranks(x, world, device="cuda"):
