@@ -11,8 +11,10 @@
 // The ordered prefix is found without sorting: the candidates' keys
 // ((gmax - gain) << idbits | id, unique, ascending = gain desc, id asc) are radix-selected by
 // their cumulative weight (8-bit digits, most significant first) in one CTA.  All round control
-// lives in a device block (RefineCtl), so a level's rounds are enqueued without host round trips;
-// kernels of rounds after the stop return at once.
+// lives in a device block (Ctl), so a level's rounds run without host round trips: the levels of a
+// partition go through three launches of k_refine_tail (one CTA, one cluster, one cooperative grid,
+// by level size), and the launch-per-step kernels (whose rounds after the stop return at once)
+// remain for devices without cooperative launch.  Fixed vertices (g.fix) are never candidates.
 #pragma once
 #include "gp_internal.cuh"
 #include "k_coarsen.cuh"
