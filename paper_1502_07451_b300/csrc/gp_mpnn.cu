@@ -333,7 +333,7 @@ static void propose_split(const gp_graph* g, const float* logit, int64_t BC, int
     const int shift = 56 - 8 * p;
     GP_LAUNCH(F_PROPOSE, k_prop_hist, grid_for(n, 256, 4), 256, 0, s, n, (const unsigned long long*)key,
               (const int64_t*)g->L0.vC, (const int64_t*)g->L0.vG, (const PropSel*)dsel, shift, hist);
-    GP_LAUNCH(F_PROPOSE, k_prop_pick, 1, 32, 0, s, dsel, shift, hist);
+    GP_LAUNCH(F_PROPOSE, k_prop_pick, 1, 64, 0, s, dsel, shift, hist);
   }
   GP_CHECK_LAUNCH();
   GP_CUDA(cudaMemcpyAsync(&hs, dsel, sizeof(hs), cudaMemcpyDeviceToHost, s));

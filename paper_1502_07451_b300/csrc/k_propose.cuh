@@ -66,35 +66,56 @@ __global__ void __launch_bounds__(256) k_prop_hist(int64_t n, const unsigned lon
   }
 }
 
-// one thread: choose each selection's digit (the first where the running weight exceeds rem)
-__global__ void k_prop_pick(PropSel* sel, int shift, unsigned long long* __restrict__ hist) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  for (int q = 0; q < 2; q++) {
-    if (!sel->active[q]) continue;
+// Each selection's digit: the first where the running weight exceeds rem.  Warp q serves selection q:
+// lane l sums digits 8l..8l+7, a warp scan gives the weight before each lane's digits, and the first lane
+// whose digits pass rem walks them.  Then the histogram is cleared for the next digit (64 threads).
+__global__ void __launch_bounds__(64) k_prop_pick(PropSel* sel, int shift, unsigned long long* __restrict__ hist) {
+  const int q = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (sel->active[q]) {
     const unsigned long long* w = hist + q * 512;
     const unsigned long long* c = w + 256;
-    long long cum = 0;
-    unsigned long long below = 0;
-    int chosen = -1;
-    for (int d = 0; d < 256; d++) {
-      if (cum + (long long)w[d] > sel->rem[q]) {
-        chosen = d;
-        break;
+    long long w8 = 0;
+    unsigned long long c8 = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      w8 += (long long)w[8 * l + k];
+      c8 += c[8 * l + k];
+    }
+    long long wi = w8;
+    unsigned long long ci = c8;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long a = __shfl_up_sync(0xffffffffu, wi, o);
+      const unsigned long long b = __shfl_up_sync(0xffffffffu, ci, o);
+      if (l >= o) {
+        wi += a;
+        ci += b;
       }
-      cum += (long long)w[d];
-      below += c[d];
     }
-    if (chosen < 0) {  // the whole region fits: no crossing key
-      sel->active[q] = 0;
-      sel->found[q] = 0;
-      continue;
+    const long long rem = sel->rem[q];
+    const unsigned pass = __ballot_sync(0xffffffffu, wi > rem);
+    if (pass == 0) {  // the whole region fits: no crossing key
+      if (l == 0) {
+        sel->active[q] = 0;
+        sel->found[q] = 0;
+      }
+    } else if (l == __ffs(pass) - 1) {
+      long long cum = wi - w8;
+      unsigned long long below = ci - c8;
+      int d = 8 * l;
+      for (;; d++) {
+        if (cum + (long long)w[d] > rem) break;
+        cum += (long long)w[d];
+        below += c[d];
+      }
+      sel->prefix[q] |= (unsigned long long)d << shift;
+      sel->rem[q] -= cum;
+      sel->less[q] += below;
+      sel->found[q] = 1;
     }
-    sel->prefix[q] |= (unsigned long long)chosen << shift;
-    sel->rem[q] -= cum;
-    sel->less[q] += below;
-    sel->found[q] = 1;
   }
-  for (int i = 0; i < 1024; i++) hist[i] = 0ull;
+  __syncthreads();
+  for (int i = threadIdx.x; i < 1024; i += blockDim.x) hist[i] = 0ull;
 }
 
 // part[v] = 0 (CPU) for the first k keys: key < thr, or key <= thr when inclusive; all / none by mode
