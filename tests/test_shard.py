@@ -38,6 +38,12 @@ def test_lpt_edge_cases():
         shard.lpt([1], 0)
 
 
+def test_spec_edge_counts_match_the_built_graphs():
+    spec = gen.batch_spec(120)
+    for it in spec[::7]:
+        assert gen.spec_edges(it) == gen.build_from_spec(it)["m"], it
+
+
 def test_batch_shards_cover_the_recipe_and_balance_edges():
     sys.path.insert(0, ROOT)
     import bench
