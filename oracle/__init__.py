@@ -114,6 +114,9 @@ def lib():
             L.og_cut.argtypes = [_I64, _P, _P, _P, _P, _P]
             L.og_levels.argtypes = [_I64, _I64, _P, _P, _P, _P]
             L.og_makespan.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]
+            L.og_partition_vcycle.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
+                                              C.c_uint64, _P, _P, _P]
+            L.og_makespan_workers.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]
             L.og_propose.argtypes = [_I64, _P, _P, _P, _I64, _I64, _P, _P]
             L.og_partition_learned.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
                                                _P, _P]
@@ -318,6 +321,26 @@ def partition_learned(g, logits, r_cpu: float = -1.0, tol: float = 0.03):
     return part[:n], res.as_dict()
 
 
+def partition_vcycle(g, logits, r_cpu: float = -1.0, tol: float = 0.03, seed: int = 0, trace: bool = False):
+    """The learned path as a V-cycle: the proposal from the logits restricts the matching to
+    same-side pairs, the coarsest split is the proposed sides, and every level is refined on the way
+    back.  Returns (part, result dict[, trace dict])."""
+    off, cols, w, cc, cg = _graph_arrays(g)
+    n = g["n"]
+    lg = _c(logits, np.float32)
+    if lg.shape[0] == 0:
+        lg = np.zeros(1, np.float32)
+    part = np.zeros(max(n, 1), np.uint8)
+    res = Result()
+    tr = Trace()
+    _check(lib().og_partition_vcycle(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), _p(lg), r_cpu, tol,
+                                     seed, _p(part), C.byref(res), C.byref(tr) if trace else None),
+           "og_partition_vcycle")
+    if trace:
+        return part[:n], res.as_dict(), tr.as_dict()
+    return part[:n], res.as_dict()
+
+
 def cut(g, part) -> int:
     """Sum of transfer costs of directed edges whose ends are on different sides."""
     off, cols, w, _, _ = _graph_arrays(g)
@@ -348,6 +371,24 @@ def makespan(g, part, with_finish: bool = False):
     ms = C.c_int64()
     _check(lib().og_makespan(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), _p(part), _p(fin),
                              C.byref(ms)), "og_makespan")
+    if with_finish:
+        return int(ms.value), fin[:n]
+    return int(ms.value)
+
+
+def makespan_workers(g, part, workers_cpu: int = 3, workers_gpu: int = 1, with_finish: bool = False):
+    """Makespan of the mapping on a fixed number of workers per side (Sec. IV.A's testbed: 3 CPU
+    worker cores, 1 GPU worker): the list schedule of og_makespan_workers."""
+    off, cols, w, cc, cg = _graph_arrays(g)
+    n = g["n"]
+    part = _c(part, np.uint8)
+    if part.shape[0] == 0:
+        part = np.zeros(1, np.uint8)
+    fin = np.zeros(max(n, 1), np.int64)
+    ms = C.c_int64()
+    _check(lib().og_makespan_workers(n, g["m"], _p(off), _p(cols), _p(w), _p(cc), _p(cg), _p(part),
+                                     int(workers_cpu), int(workers_gpu), _p(fin), C.byref(ms)),
+           "og_makespan_workers")
     if with_finish:
         return int(ms.value), fin[:n]
     return int(ms.value)

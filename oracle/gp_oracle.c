@@ -811,10 +811,15 @@ static void og_level_free(og_level* L) {
   memset(L, 0, sizeof(*L));
 }
 
-int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* cols,
-                       const int32_t* w, const int32_t* cC, const int32_t* cG, const int8_t* fixed,
-                       double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
-                       og_trace* trace) {
+/* The multilevel bipartitioner.  fixed: NULL (all free), or one pin per vertex (-1 free, 0 CPU,
+ * 1 GPU).  restrict_only = 0: the pins hold through every step (fixed vertices).  restrict_only = 1
+ * (the V-cycle from a proposed split; every vertex carries its proposed side): the pins only keep
+ * the matching to same-side pairs, the coarsest level's split is its pins, and refinement moves any
+ * vertex. */
+static int og_multilevel(int64_t n, int64_t m, const int64_t* off, const int32_t* cols,
+                         const int32_t* w, const int32_t* cC, const int32_t* cG, const int8_t* fixed,
+                         int restrict_only, double r_cpu, double tol, uint64_t seed, uint8_t* part,
+                         og_result* res, og_trace* trace) {
   int st = og_validate(n, m, off, cols, w, cC, cG);
   if (st != OG_OK) return st;
   if (fixed)
@@ -913,9 +918,12 @@ int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* 
   pc = (uint8_t*)malloc((size_t)lv[L].n);
   if (!pc) goto done;
   int32_t trial = -1;
-  if (og_gggp_fix(lv[L].n, lv[L].off, lv[L].adj, lv[L].W, lv[L].vC, lv[L].vG, lv[L].fix, BC, BG,
-                  seed, pc, &trial) != OG_OK)
+  if (restrict_only) { /* every coarse vertex holds members of one proposed side */
+    for (int64_t x = 0; x < lv[L].n; x++) pc[x] = (uint8_t)lv[L].fix[x];
+  } else if (og_gggp_fix(lv[L].n, lv[L].off, lv[L].adj, lv[L].W, lv[L].vC, lv[L].vG, lv[L].fix, BC, BG,
+                         seed, pc, &trial) != OG_OK) {
     goto done;
+  }
 
   /* uncoarsening */
   int32_t rounds_total = 0;
@@ -930,8 +938,8 @@ int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* 
       pc = pf;
       pf = NULL;
     }
-    if (og_refine_fix(lv[l].n, lv[l].off, lv[l].adj, lv[l].W, lv[l].vC, lv[l].vG, lv[l].fix, BC,
-                      BG, pc, &rs) != OG_OK)
+    if (og_refine_fix(lv[l].n, lv[l].off, lv[l].adj, lv[l].W, lv[l].vC, lv[l].vG,
+                      restrict_only ? NULL : lv[l].fix, BC, BG, pc, &rs) != OG_OK)
       goto done;
     rounds_total += rs.rounds;
     if (trace) {
@@ -964,6 +972,13 @@ done:
   free(pf);
   for (int l = 0; l <= OG_MAX_LEVELS; l++) og_level_free(&lv[l]);
   return rc;
+}
+
+int og_partition_fixed(int64_t n, int64_t m, const int64_t* off, const int32_t* cols,
+                       const int32_t* w, const int32_t* cC, const int32_t* cG, const int8_t* fixed,
+                       double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
+                       og_trace* trace) {
+  return og_multilevel(n, m, off, cols, w, cC, cG, fixed, 0, r_cpu, tol, seed, part, res, trace);
 }
 
 int og_partition(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
@@ -1184,5 +1199,187 @@ done:
   free(uW);
   free(vC);
   free(vG);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Makespan of a mapping on a fixed number of workers per side (the testbed   */
+/* of Sec. IV.A runs kernels on 3 CPU worker cores and 1 GPU worker): a list  */
+/* schedule, simulated event by event in time order.                          */
+/*                                                                           */
+/*   - A task v runs without preemption on one worker of side part[v] for    */
+/*     its cost on that side; each side has its own workers (P_C, P_G).      */
+/*   - Its data are there at r(v) = max over in-entries u->v of finish(u),   */
+/*     plus w(u,v) when u sits on the other side (every parallel entry is a  */
+/*     transfer of its own; transfers do not compete); r = 0 for a source.   */
+/*   - At each time t, in increasing order: first every running task that    */
+/*     ends at or before t ends (its worker becomes idle, and each successor */
+/*     whose last predecessor this was is released); then, on each side,     */
+/*     while a worker is idle and a released task with r <= t waits, the     */
+/*     waiting task with the smallest (r, id) starts at t.  t then moves to  */
+/*     the next end of a running task or, on a side with an idle worker, to  */
+/*     the smallest r among its waiting tasks, whichever comes first.        */
+/*   - makespan = the largest finish time (0 for an empty graph).            */
+/* Identical idle workers are interchangeable, so the times do not depend on */
+/* which idle worker takes a task.  With at least n workers on both sides    */
+/* every task starts at r(v) and the result is og_makespan's.                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t t;  /* ready time (waiting heaps) or end time (running heap) */
+  int32_t v;
+} og_ev;
+
+static int og_ev_less(const og_ev* a, const og_ev* b) {
+  return a->t < b->t || (a->t == b->t && a->v < b->v);
+}
+
+static void og_heap_push(og_ev* h, int64_t* len, og_ev x) {
+  int64_t i = (*len)++;
+  while (i > 0) {
+    const int64_t p = (i - 1) / 2;
+    if (!og_ev_less(&x, &h[p])) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i] = x;
+}
+
+static og_ev og_heap_pop(og_ev* h, int64_t* len) {
+  const og_ev top = h[0];
+  const og_ev x = h[--(*len)];
+  int64_t i = 0;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= *len) break;
+    if (c + 1 < *len && og_ev_less(&h[c + 1], &h[c])) c++;
+    if (!og_ev_less(&h[c], &x)) break;
+    h[i] = h[c];
+    i = c;
+  }
+  if (*len > 0) h[i] = x;
+  return top;
+}
+
+int og_makespan_workers(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                        const int32_t* cC, const int32_t* cG, const uint8_t* part, int64_t workers_cpu,
+                        int64_t workers_gpu, int64_t* finish, int64_t* makespan) {
+  int st = og_validate(n, m, off, cols, w, cC, cG);
+  if (st != OG_OK) return st;
+  if (workers_cpu < 1 || workers_gpu < 1) return OG_ERR_INVALID;
+  for (int64_t v = 0; v < n; v++)
+    if (part[v] > 1) return OG_ERR_INVALID;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t* pending = (int64_t*)calloc(nn, sizeof(int64_t));
+  int64_t* ready = (int64_t*)calloc(nn, sizeof(int64_t));
+  int64_t* fin = (int64_t*)calloc(nn, sizeof(int64_t));
+  og_ev* wait[2] = {(og_ev*)malloc(nn * sizeof(og_ev)), (og_ev*)malloc(nn * sizeof(og_ev))};
+  og_ev* run = (og_ev*)malloc(nn * sizeof(og_ev));
+  if (!pending || !ready || !fin || !wait[0] || !wait[1] || !run) {
+    free(pending);
+    free(ready);
+    free(fin);
+    free(wait[0]);
+    free(wait[1]);
+    free(run);
+    return OG_ERR_OOM;
+  }
+  for (int64_t e = 0; e < m; e++) pending[cols[e]]++;
+  int64_t wlen[2] = {0, 0}, rlen = 0;
+  int64_t idle[2] = {workers_cpu, workers_gpu};
+  for (int64_t v = 0; v < n; v++)
+    if (pending[v] == 0) {
+      og_ev x = {0, (int32_t)v};
+      og_heap_push(wait[part[v]], &wlen[part[v]], x);
+    }
+  int64_t t = 0, ms = 0;
+  for (;;) {
+    /* ends at or before t */
+    while (rlen > 0 && run[0].t <= t) {
+      const og_ev done = og_heap_pop(run, &rlen);
+      const int32_t u = done.v;
+      idle[part[u]]++;
+      for (int64_t e = off[u]; e < off[u + 1]; e++) {
+        const int32_t v = cols[e];
+        const int64_t arrive = fin[u] + (part[u] != part[v] ? w[e] : 0);
+        if (arrive > ready[v]) ready[v] = arrive;
+        if (--pending[v] == 0) {
+          og_ev x = {ready[v], v};
+          og_heap_push(wait[part[v]], &wlen[part[v]], x);
+        }
+      }
+    }
+    /* starts at t */
+    for (int s = 0; s < 2; s++)
+      while (idle[s] > 0 && wlen[s] > 0 && wait[s][0].t <= t) {
+        const og_ev x = og_heap_pop(wait[s], &wlen[s]);
+        const int32_t v = x.v;
+        fin[v] = t + (part[v] ? cG[v] : cC[v]);
+        if (fin[v] > ms) ms = fin[v];
+        og_ev r = {fin[v], v};
+        og_heap_push(run, &rlen, r);
+        idle[s]--;
+      }
+    if (rlen > 0 && run[0].t <= t) continue; /* a task of cost 0 ended at t */
+    int64_t next = INT64_MAX;
+    if (rlen > 0) next = run[0].t;
+    for (int s = 0; s < 2; s++)
+      if (idle[s] > 0 && wlen[s] > 0 && wait[s][0].t < next) next = wait[s][0].t;
+    if (next == INT64_MAX) break;
+    t = next;
+  }
+  if (finish)
+    for (int64_t v = 0; v < n; v++) finish[v] = fin[v];
+  *makespan = ms;
+  free(pending);
+  free(ready);
+  free(fin);
+  free(wait[0]);
+  free(wait[1]);
+  free(run);
+  return OG_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The learned path as a V-cycle: the proposal from the logits (og_propose)  */
+/* gives every vertex a side; coarsening matches only vertices proposed to   */
+/* the same side (the proposal's sides are pins for the matching and the     */
+/* two-hop pairing only), so every coarse vertex has one proposed side, and  */
+/* the coarsest level's split is those sides; then every level is refined    */
+/* on the way back up exactly as in og_partition (projection, balance round, */
+/* gain rounds, with every vertex free to move).                             */
+/* ------------------------------------------------------------------------ */
+int og_partition_vcycle(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                        const int32_t* cC, const int32_t* cG, const float* logits, double r_cpu,
+                        double tol, uint64_t seed, uint8_t* part, og_result* res, og_trace* trace) {
+  int st = og_validate(n, m, off, cols, w, cC, cG);
+  if (st != OG_OK) return st;
+  int64_t SC = 0, SG = 0;
+  for (int64_t v = 0; v < n; v++) {
+    SC += cC[v];
+    SG += cG[v];
+  }
+  int64_t BC, BG;
+  st = og_bounds(SC, SG, r_cpu, tol, &BC, &BG);
+  if (st != OG_OK) return st;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t* vC = (int64_t*)malloc(nn * sizeof(int64_t));
+  int64_t* vG = (int64_t*)malloc(nn * sizeof(int64_t));
+  uint8_t* prop = (uint8_t*)malloc(nn);
+  int8_t* pin = (int8_t*)malloc(nn);
+  int rc = OG_ERR_OOM;
+  if (!vC || !vG || !prop || !pin) goto done;
+  for (int64_t v = 0; v < n; v++) {
+    vC[v] = cC[v];
+    vG[v] = cG[v];
+  }
+  rc = og_propose(n, logits, vC, vG, BC, BG, prop, NULL);
+  if (rc != OG_OK) goto done;
+  for (int64_t v = 0; v < n; v++) pin[v] = (int8_t)prop[v];
+  rc = og_multilevel(n, m, off, cols, w, cC, cG, pin, 1, r_cpu, tol, seed, part, res, trace);
+done:
+  free(vC);
+  free(vG);
+  free(prop);
+  free(pin);
   return rc;
 }

@@ -140,12 +140,29 @@ int og_partition_learned(int64_t n, int64_t m, const int64_t* off, const int32_t
                          const int32_t* cpu_cost, const int32_t* gpu_cost, const float* logits,
                          double r_cpu, double tol, uint8_t* part, og_result* res);
 
+/* The learned path as a V-cycle (restricted coarsening): the proposal's sides restrict the
+ * matching to same-side pairs, the coarsest level takes the proposed sides as its split, and every
+ * level is refined on the way back (og_partition's uncoarsening, every vertex free). */
+int og_partition_vcycle(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                        const int32_t* cpu_cost, const int32_t* gpu_cost, const float* logits,
+                        double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
+                        og_trace* trace);
+
 int og_levels(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, int32_t* level,
               int32_t* nlevels);
 
 int og_makespan(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
                 const int32_t* cpu_cost, const int32_t* gpu_cost, const uint8_t* part,
                 int64_t* finish, int64_t* makespan);
+
+/* Makespan of a mapping on workers_cpu CPU workers and workers_gpu GPU workers (each >= 1; the
+ * testbed of Sec. IV.A has 3 and 1): a non-preemptive list schedule simulated in time order.  A task
+ * is released when its last predecessor ends and has its data at r(v) (og_makespan's start time);
+ * whenever a worker of a side is idle, the released task of that side with the smallest (r, id) and
+ * r <= now starts on it.  finish (nullable) receives every task's end time. */
+int og_makespan_workers(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                        const int32_t* cpu_cost, const int32_t* gpu_cost, const uint8_t* part,
+                        int64_t workers_cpu, int64_t workers_gpu, int64_t* finish, int64_t* makespan);
 
 #ifdef __cplusplus
 }

@@ -55,3 +55,53 @@ def longest_path_makespan(g, part):
             u = int(cols[e])
             stack.append((u, t + (int(w[e]) if part[u] != part[v] else 0) + cost[u]))
     return best
+
+
+def list_schedule_stepped(g, part, workers_cpu, workers_gpu):
+    """The list schedule on P_C CPU and P_G GPU workers, simulated one time unit at a time (integer
+    costs; tiny graphs only).  At every integer time t: tasks that end at t end and release the
+    successors whose predecessors have all ended, then every idle worker takes the released task of
+    its side with the smallest (data arrival, id) among those whose data have arrived; a task of cost 0
+    ends at once, so both steps repeat until nothing changes at t.  Returns (makespan, finish list)."""
+    n = g["n"]
+    off, cols, w = g["offsets"], g["cols"], g["edge_cost"]
+    cost = [int(g["gpu_cost"][v]) if part[v] else int(g["cpu_cost"][v]) for v in range(n)]
+    npred = [0] * n
+    for e in range(int(off[n])):
+        npred[int(cols[e])] += 1
+    arrive = [0] * n
+    released = {v for v in range(n) if npred[v] == 0}
+    started = set()
+    ended = set()
+    end = [None] * n
+    idle = [workers_cpu, workers_gpu]
+    t = 0
+    limit = sum(cost) + int(np.asarray(w).sum()) + 1
+    while len(ended) < n:
+        assert t <= limit, "no progress"
+        changed = True
+        while changed:
+            changed = False
+            for u in range(n):
+                if u in started and u not in ended and end[u] == t:
+                    ended.add(u)
+                    idle[part[u]] += 1
+                    changed = True
+                    for e in range(int(off[u]), int(off[u + 1])):
+                        v = int(cols[e])
+                        arrive[v] = max(arrive[v], t + (int(w[e]) if part[u] != part[v] else 0))
+                        npred[v] -= 1
+                        if npred[v] == 0:
+                            released.add(v)
+            for s in (0, 1):
+                while idle[s] > 0:
+                    ready = [(arrive[v], v) for v in released if part[v] == s and v not in started and arrive[v] <= t]
+                    if not ready:
+                        break
+                    _, v = min(ready)
+                    started.add(v)
+                    end[v] = t + cost[v]
+                    idle[s] -= 1
+                    changed = True
+        t += 1
+    return (max(end) if n else 0), end
