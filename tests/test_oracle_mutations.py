@@ -52,6 +52,19 @@ MUTATIONS = {
     "fixed_balance_moves_pins": ("if (part[v] == s && !(fix && fix[v] >= 0)) {", "if (part[v] == s) {"),
     "fixed_grow_region_empty": ("    side[v] = (fix && fix[v] == 0) ? 0 : 1;\n    toC[v] = 0;",
                                 "    side[v] = 1;\n    toC[v] = 0;"),
+    "listsched_ignores_transfer": ("const int64_t arrive = fin[u] + (part[u] != part[v] ? w[e] : 0);",
+                                   "const int64_t arrive = fin[u];"),
+    "listsched_starts_before_data": ("while (idle[s] > 0 && wlen[s] > 0 && wait[s][0].t <= t) {",
+                                     "while (idle[s] > 0 && wlen[s] > 0) {"),
+    "listsched_ties_larger_id_first": ("return a->t < b->t || (a->t == b->t && a->v < b->v);",
+                                       "return a->t < b->t || (a->t == b->t && a->v > b->v);"),
+    "listsched_order_by_id_only": ("return a->t < b->t || (a->t == b->t && a->v < b->v);", "return a->v < b->v;"),
+    "listsched_worker_never_freed": ("      idle[part[u]]++;\n", ""),
+    "listsched_wrong_side_cost": ("fin[v] = t + (part[v] ? cG[v] : cC[v]);", "fin[v] = t + (part[v] ? cC[v] : cG[v]);"),
+    "vcycle_refine_keeps_pins": ("                      restrict_only ? NULL : lv[l].fix, BC, BG, pc, &rs) != OG_OK)",
+                                 "                      lv[l].fix, BC, BG, pc, &rs) != OG_OK)"),
+    "vcycle_coarsest_all_gpu": ("for (int64_t x = 0; x < lv[L].n; x++) pc[x] = (uint8_t)lv[L].fix[x];",
+                                "for (int64_t x = 0; x < lv[L].n; x++) pc[x] = 1;"),
     "no_twohop_in_pipeline": ("        og_match_twohop_fix(f->n, f->off, f->adj, f->W, f->vC, f->vG, f->fix, capC, capG, seed,\n"
                               "                            mate) != OG_OK) {", "        0) {"),
 }

@@ -618,3 +618,154 @@ def test_oracle_regression_record(oracle_mod):
         c = rec[name]
         assert res == c["result"] and np.packbits(part).tobytes().hex() == c["part_hex"], name
         assert oracle_mod.makespan(g, part) == c["makespan"] and tr["n"] == c["levels_n"], name
+
+
+# ---------------------------------------------------------------------------
+# Makespan on a fixed number of workers (list schedule; Sec. IV.A's 3 CPU + 1 GPU workers)
+# ---------------------------------------------------------------------------
+
+def test_makespan_workers_hand_examples(oracle_mod):
+    for ex in load("hand_examples.json")["makespan_workers"]:
+        g = gen.from_edges(ex["n"], ex["edges"], ex["cpu"], ex["gpu"], ex["w"])
+        part = np.array(ex["part"], np.uint8)
+        ms, fin = oracle_mod.makespan_workers(g, part, ex["workers_cpu"], ex["workers_gpu"], with_finish=True)
+        assert ms == ex["makespan"], ex["name"]
+        assert fin.tolist() == ex["finish"], ex["name"]
+        assert oracle_mod.makespan(g, part) == ex["unbounded_makespan"], ex["name"]
+
+
+def test_makespan_workers_unbounded_is_the_longest_path(oracle_mod):
+    """With a worker for every task on both sides, every task starts when its data arrive: the
+    finish times are those of the longest-path makespan."""
+    for seed in range(30):
+        g = gen.random_dag(40 + seed, 120 + 3 * seed, seed)
+        rng = np.random.default_rng(seed)
+        for _ in range(3):
+            part = rng.integers(0, 2, g["n"]).astype(np.uint8)
+            ms, fin = oracle_mod.makespan(g, part, with_finish=True)
+            ms2, fin2 = oracle_mod.makespan_workers(g, part, g["n"], g["n"], with_finish=True)
+            assert ms2 == ms and np.array_equal(fin, fin2)
+
+
+def test_makespan_workers_one_worker_runs_back_to_back(oracle_mod):
+    """One worker and every task on its side: no transfers, and the worker is never idle while a
+    task is left (some unfinished task always has all its predecessors done), so the makespan is the
+    sum of the costs."""
+    for seed in range(20):
+        g = gen.random_dag(50, 150, seed)
+        n = g["n"]
+        assert oracle_mod.makespan_workers(g, np.zeros(n, np.uint8), 1, 5) == int(g["cpu_cost"].sum())
+        assert oracle_mod.makespan_workers(g, np.ones(n, np.uint8), 7, 1) == int(g["gpu_cost"].sum())
+
+
+def test_makespan_workers_equals_time_stepped_simulation(oracle_mod):
+    """Tiny DAGs with small integer costs (zeros included): the event-driven schedule equals a
+    schedule simulated one time unit at a time."""
+    for seed in range(60):
+        rng = np.random.default_rng(1000 + seed)
+        n = int(rng.integers(2, 11))
+        pairs = [(u, v) for u in range(n) for v in range(u + 1, n)]
+        k = int(rng.integers(0, min(len(pairs), 18) + 1))
+        idx = rng.choice(len(pairs), size=k, replace=False) if k else []
+        edges = [pairs[i] for i in idx]
+        if seed % 5 == 0 and edges:
+            edges.append(edges[0])  # a parallel entry
+        g = gen.from_edges(n, edges, rng.integers(0, 7, n).tolist(), rng.integers(0, 7, n).tolist(),
+                           rng.integers(0, 7, len(edges)).tolist())
+        for pc, pg in ((1, 1), (2, 1), (3, 1), (1, 2)):
+            part = rng.integers(0, 2, n).astype(np.uint8)
+            ms, fin = oracle_mod.makespan_workers(g, part, pc, pg, with_finish=True)
+            bms, bfin = _brute.list_schedule_stepped(g, part, pc, pg)
+            assert ms == bms and fin.tolist() == bfin, (seed, pc, pg)
+
+
+def test_makespan_workers_bounds(oracle_mod):
+    """longest path <= makespan; load of a side / its workers <= makespan; makespan <= all costs +
+    all transfers."""
+    for seed in range(20):
+        g = gen.random_dag(60, 200, seed)
+        rng = np.random.default_rng(seed)
+        for pc, pg in ((3, 1), (2, 2), (1, 1)):
+            part = rng.integers(0, 2, g["n"]).astype(np.uint8)
+            ms = oracle_mod.makespan_workers(g, part, pc, pg)
+            lc = int(g["cpu_cost"][part == 0].sum())
+            lg = int(g["gpu_cost"][part == 1].sum())
+            assert ms >= oracle_mod.makespan(g, part)
+            assert ms * pc >= lc and ms * pg >= lg
+            assert ms <= lc + lg + int(g["edge_cost"].sum())
+
+
+def test_makespan_workers_rejects_bad_arguments(oracle_mod):
+    g = gen.cholesky(4)
+    part = np.zeros(g["n"], np.uint8)
+    for pc, pg in ((0, 1), (1, 0)):
+        with pytest.raises(oracle_mod.OracleError):
+            oracle_mod.makespan_workers(g, part, pc, pg)
+    part[3] = 2
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.makespan_workers(g, part, 3, 1)
+    empty = gen.from_edges(0, [], [], [], [])
+    assert oracle_mod.makespan_workers(empty, np.zeros(0, np.uint8), 3, 1) == 0
+
+
+# ---------------------------------------------------------------------------
+# The learned path as a V-cycle (restricted coarsening)
+# ---------------------------------------------------------------------------
+
+def _noisy_logits(g, oracle_mod, seed, scale=0.8):
+    """Logits a trained network might give: the plain split's sides (CPU positive) plus noise."""
+    p0, _ = oracle_mod.partition(g)
+    rng = np.random.default_rng(seed)
+    return (np.where(p0 == 0, 1.0, -1.0) + rng.normal(0.0, scale, g["n"])).astype(np.float32)
+
+
+def test_vcycle_all_gpu_proposal_is_the_plain_partition(oracle_mod):
+    """When all-GPU fits (SG <= B_G) the proposal is all-GPU, so the restriction is void: the
+    V-cycle's coarsening, coarsest split (all-GPU, the growing's pre-check) and refinement are the
+    plain partition's, result for result."""
+    for seed in range(6):
+        g = gen.layered(30, 40, 3000, seed, ratio_lo=60.0, ratio_hi=80.0)
+        sc, sg = int(g["cpu_cost"].sum()), int(g["gpu_cost"].sum())
+        _, bg = oracle_mod.bounds(sc, sg)
+        assert sg <= bg
+        lg = np.random.default_rng(seed).normal(0, 1, g["n"]).astype(np.float32)
+        pv, rv, tv = oracle_mod.partition_vcycle(g, lg, seed=seed, trace=True)
+        pp, rp, tp = oracle_mod.partition(g, seed=seed, trace=True)
+        assert np.array_equal(pv, pp) and rv == rp
+        assert tv["n"] == tp["n"] and tv["a"] == tp["a"] and tv["levels"] > 0
+
+
+def test_vcycle_never_worse_than_a_feasible_proposal(oracle_mod):
+    """The coarsest split is the proposal itself (a coarse vertex holds one proposed side, so the
+    projection keeps its cut and loads); a feasible split needs no balance round and gain rounds
+    never raise the cut: the result is feasible, its cut at most the proposal's, and strictly below
+    it on noisy proposals (refinement at the coarse levels moves whole clusters)."""
+    lower = 0
+    for seed, g in enumerate([gen.layered(40, 150, 40000, 7), gen.cholesky(20), gen.lu(16),
+                              gen.layered(60, 300, 120000, 3), gen.random_dag(3000, 12000, 4)]):
+        lg = _noisy_logits(g, oracle_mod, seed)
+        cc, cg = g["cpu_cost"].astype(np.int64), g["gpu_cost"].astype(np.int64)
+        bc, bg = oracle_mod.bounds(int(cc.sum()), int(cg.sum()))
+        prop, _ = oracle_mod.propose(lg, cc, cg, bc, bg)
+        feasible = cc[prop == 0].sum() <= bc and cg[prop == 1].sum() <= bg
+        part, res, tr = oracle_mod.partition_vcycle(g, lg, trace=True)
+        assert res["cut"] == oracle_mod.cut(g, part)
+        assert res["load_cpu"] == int(cc[part == 0].sum()) and res["load_gpu"] == int(cg[part == 1].sum())
+        if feasible:
+            assert res["feasible"] == 1 and sum(tr["balanced"]) == 0
+            # level by level (coarsest first) the refined cut only falls, from the proposal's
+            cuts = [oracle_mod.cut(g, prop)] + tr["cut"][::-1]
+            assert all(a >= b for a, b in zip(cuts, cuts[1:])), cuts
+            assert res["cut"] <= oracle_mod.cut(g, prop)
+            lower += res["cut"] < oracle_mod.cut(g, prop)
+    assert lower >= 3
+
+
+def test_vcycle_coarsens_through_levels_and_reports_them(oracle_mod):
+    g = gen.layered(60, 300, 120000, 3)
+    lg = _noisy_logits(g, oracle_mod, 9)
+    part, res, tr = oracle_mod.partition_vcycle(g, lg, trace=True)
+    assert res["levels"] == tr["levels"] > 3 and tr["gggp_trial"] == -1
+    assert tr["n"][0] == g["n"] and res["coarsest_n"] == tr["n"][-1]
+    assert all(a > b for a, b in zip(tr["n"], tr["n"][1:]))
+    assert sum(tr["rounds"]) == res["rounds"]
