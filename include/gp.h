@@ -200,20 +200,51 @@ GP_API gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* ma
                       void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * gp_makespan_workers -- makespan of a mapping on a fixed number of workers per side.  The paper's
+ * testbed runs the kernels on 3 CPU worker cores and 1 GPU worker (Sec. IV.A); gp_makespan assumes as
+ * many workers as a level needs.  Here every task runs without preemption on one worker of its side
+ * for its cost there; its data are there at r(v) = max over in-entries u->v of finish(u) (+ w(u,v)
+ * when u is on the other side; every parallel entry counts, transfers do not compete); whenever a
+ * worker of a side is idle, the released task of that side with the smallest (r, id) and r <= now
+ * starts on it (a list schedule, simulated event by event in time order).  With at least n workers
+ * per side the result is gp_makespan's.
+ *   part          uint8[n], device or host (0 = CPU, 1 = GPU)
+ *   workers_cpu   CPU workers, >= 1; workers_gpu: GPU workers, >= 1; workers_cpu + workers_gpu <= 32
+ *   makespan      host int64, receives the largest finish time (0 for an empty graph)
+ *   finish_out    int64[n] (device or host) or NULL: every task's finish time
+ * The simulation of one graph is sequential (one warp); see gp_batch_makespan_workers for many.
+ * Errors: GP_ERR_INVALID (worker counts, part[v] > 1, handle on another device), GP_ERR_OOM,
+ * GP_ERR_CUDA, GP_ERR_TIMEOUT (the event loop exceeded its iteration bound).
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_makespan_workers(const gp_graph* g, const uint8_t* part, int32_t workers_cpu,
+                                     int32_t workers_gpu, int64_t* makespan, int64_t* finish_out, void* stream);
+
+/* gp_makespan_workers for `count` graphs in one persistent launch (one warp per graph, largest
+ * first): parts[i] uint8[n_i] (device or host), makespans int64[count] (host).  Results equal
+ * gp_makespan_workers graph by graph. */
+GP_API gp_status gp_batch_makespan_workers(int32_t count, gp_graph* const* graphs, const uint8_t* const* parts,
+                                           int32_t workers_cpu, int32_t workers_gpu, int64_t* makespans,
+                                           void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * gp_makespan_noalloc -- the same result as gp_makespan, for callers that cannot allocate device
  * memory (the paper has no counterpart: this is a deployment variant).  gp_makespan takes its
- * per-call scratch from the device memory pool; callers that run inside a stream capture that
- * forbids allocation, in latency-critical loops, or under a host allocator that owns all device
- * memory cannot let it.  This variant uses a scratch array compiled into the library (8 MiB + 64
- * bytes per GPU that loads the library, held until the process exits) and allocates nothing.
+ * per-call scratch from the device memory pool.  Hosts that give all device memory to their own
+ * allocator at start-up and let no one else allocate (a serving process with its own arenas, a
+ * runtime that embeds this library in a fixed memory budget), and latency-critical loops that must
+ * not stall on or fail in an allocation, cannot let it.  This variant uses a scratch array compiled
+ * into the library (8 MiB + 64 bytes per GPU that loads the library, held until the process exits)
+ * and allocates nothing.
  *   g           handle on the current device (GP_ERR_INVALID otherwise)
  *   part        uint8[n] in DEVICE memory (0/1)
  *   makespan    host int64, receives the result
  *   finish_out  int64[n] in DEVICE memory, or NULL
+ * The call reads the result back to the host: it synchronises `stream` before it returns.
  * Limits: n <= GP_MAKESPAN_NOALLOC_MAX_N, else GP_ERR_INVALID before any work.  All calls on a GPU
- * share the one scratch array: calls whose work overlaps on that GPU (other streams or threads)
- * race; serialise them.  The first call on each device looks up the array's device address;
- * make that first call before any stream capture begins.
+ * share the one scratch array, which keeps the last call's contents: calls whose work overlaps on
+ * that GPU (other streams or threads) race; serialise them.  The first call on each device (and the
+ * first after that device's context was reset) looks up the array's device address; make that first
+ * call before any stream capture begins.
  * Errors: GP_ERR_INVALID (limits, host pointers, part[v] > 1), GP_ERR_CUDA, GP_ERR_TIMEOUT.
  * ------------------------------------------------------------------------------------------- */
 #define GP_MAKESPAN_NOALLOC_MAX_N (1 << 20)
@@ -368,6 +399,17 @@ GP_API gp_status gp_model_train_step(gp_model* m, const gp_graph* g, const uint8
  * ms[0..2] = network, proposal, refinement + cut (when profiling is on). */
 GP_API gp_status gp_partition_learned(gp_graph* g, const gp_model* m, const float* logits, double r_cpu,
                                       double tol, uint8_t* part_out, gp_result* res, void* stream);
+
+/* The learned path as a V-cycle (restricted coarsening): the network's proposal (as above) gives
+ * every vertex a side; coarsening matches only vertices proposed to the same side (the sides act as
+ * pins for the handshake matching and the two-hop pairing only), so every coarse vertex has one
+ * proposed side and the coarsest level takes those sides as its split; every level is then refined
+ * on the way back exactly as in gp_partition (projection, balance round, gain rounds, every vertex
+ * free).  Arguments as gp_partition_learned, plus `seed` (the matching's tie-break hash, as in
+ * gp_partition).  res->ms[4] holds the network and proposal time when profiling is on. */
+GP_API gp_status gp_partition_learned_vcycle(gp_graph* g, const gp_model* m, const float* logits, double r_cpu,
+                                             double tol, uint64_t seed, uint8_t* part_out, gp_result* res,
+                                             void* stream);
 
 /* The learned path for `count` graphs: one network forward over the disjoint union of the graphs,
  * then, per graph, exactly what gp_partition_learned(graphs[i], m, NULL, r_cpu[i], tol, ...) gives
