@@ -116,6 +116,8 @@ def lib():
             L.og_makespan.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]
             L.og_partition_vcycle.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
                                               C.c_uint64, _P, _P, _P]
+            L.og_partition_kway.argtypes = [_I64, _I64, _P, _P, _P, C.c_int32, _P, C.c_double, C.c_uint64, _P, _P,
+                                            _P, _P, _P]
             L.og_makespan_workers.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I64, _P, _P]
             L.og_propose.argtypes = [_I64, _P, _P, _P, _I64, _I64, _P, _P]
             L.og_partition_learned.argtypes = [_I64, _I64, _P, _P, _P, _P, _P, _P, C.c_double, C.c_double,
@@ -392,3 +394,24 @@ def makespan_workers(g, part, workers_cpu: int = 3, workers_gpu: int = 1, with_f
     if with_finish:
         return int(ms.value), fin[:n]
     return int(ms.value)
+
+
+def partition_kway(g, costs, tol: float = 0.03, seed: int = 0):
+    """k device classes by recursive bisection: costs is int32 [k, n] (v's time on class i).  Returns
+    (cls uint8[n], dict(cut, loads (list of k), feasible, bisections))."""
+    off, cols, w, _, _ = _graph_arrays(g)
+    n = g["n"]
+    cs = np.ascontiguousarray(np.asarray(costs, dtype=np.int32))
+    k = int(cs.shape[0])
+    if cs.ndim != 2 or cs.shape[1] != n:
+        raise ValueError("costs must be [k, n]")
+    flat = cs.reshape(-1) if cs.size else np.zeros(1, np.int32)
+    cls = np.zeros(max(n, 1), np.uint8)
+    cut_ = C.c_int64()
+    loads = np.zeros(max(k, 1), np.int64)
+    feas = C.c_int32()
+    nb = C.c_int32()
+    _check(lib().og_partition_kway(n, g["m"], _p(off), _p(cols), _p(w), k, _p(flat), tol, seed, _p(cls),
+                                   C.byref(cut_), _p(loads), C.byref(feas), C.byref(nb)), "og_partition_kway")
+    return cls[:n], dict(cut=int(cut_.value), loads=[int(x) for x in loads[:k]], feasible=int(feas.value),
+                         bisections=int(nb.value))

@@ -1383,3 +1383,127 @@ done:
   free(pin);
   return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* k device classes by recursive bisection (Sec. VI names a third kind of    */
+/* processor, an FPGA, as future work; this is the project's reading).        */
+/*                                                                           */
+/*   - costs[i * n + v] is v's time on class i (int32, >= 0); a transfer     */
+/*     between any two different classes costs w(e).                         */
+/*   - Two groups of classes act as two devices: a group's time for v is the */
+/*     classes' times combined like parallel resistors, folded left to       */
+/*     right with comb(x, y) = floor(x*y / (x+y)) (0 when x + y = 0); for    */
+/*     one class it is that class's time.  (k = 2 is then the 2-way problem  */
+/*     with c_CPU = costs[0], c_GPU = costs[1].)                             */
+/*   - bisect(V', [lo, hi)): one class left -> every vertex of V' gets it.   */
+/*     Otherwise mid = lo + ceil((hi - lo) / 2); the subgraph induced by V'  */
+/*     (vertices renumbered in increasing id, every entry with both ends in  */
+/*     V' kept) is split by og_partition with cpu_cost = the group time of   */
+/*     [lo, mid), gpu_cost = that of [mid, hi), the bounds of Eq. (1) from   */
+/*     their sums, tolerance tol and `seed`; side 0 recurses into [lo, mid), */
+/*     side 1 into [mid, hi).  An empty side ends its branch.                */
+/*   - Outputs: cls[v]; the cut (sum of w over directed entries whose ends   */
+/*     have different classes); loads[i] = sum of costs[i][v] over class-i   */
+/*     vertices; feasible = every bisection was feasible; the number of      */
+/*     bisections run.                                                       */
+/* ------------------------------------------------------------------------ */
+static int64_t og_comb(int64_t x, int64_t y) {
+  if (x + y == 0) return 0;
+  return (int64_t)(((__int128)x * (__int128)y) / (__int128)(x + y));
+}
+
+static int og_bisect(int64_t n, const int64_t* off, const int32_t* cols, const int32_t* w, int64_t n_all,
+                     const int32_t* costs, const int32_t* orig, int lo, int hi, double tol, uint64_t seed,
+                     uint8_t* cls, int32_t* feasible, int32_t* count) {
+  if (n == 0) return OG_OK;
+  if (hi - lo == 1) {
+    for (int64_t v = 0; v < n; v++) cls[orig[v]] = (uint8_t)lo;
+    return OG_OK;
+  }
+  const int mid = lo + (hi - lo + 1) / 2;
+  const size_t nn = (size_t)n;
+  int32_t* cA = (int32_t*)malloc(nn * sizeof(int32_t));
+  int32_t* cB = (int32_t*)malloc(nn * sizeof(int32_t));
+  uint8_t* part = (uint8_t*)malloc(nn);
+  int rc = OG_ERR_OOM;
+  int64_t* soff = NULL;
+  int32_t *scols = NULL, *sw = NULL, *sorig = NULL, *newid = NULL;
+  if (!cA || !cB || !part) goto done;
+  for (int64_t v = 0; v < n; v++) {
+    int64_t a = costs[(int64_t)lo * n_all + orig[v]];
+    for (int c = lo + 1; c < mid; c++) a = og_comb(a, costs[(int64_t)c * n_all + orig[v]]);
+    int64_t b = costs[(int64_t)mid * n_all + orig[v]];
+    for (int c = mid + 1; c < hi; c++) b = og_comb(b, costs[(int64_t)c * n_all + orig[v]]);
+    cA[v] = (int32_t)a;
+    cB[v] = (int32_t)b;
+  }
+  og_result res;
+  rc = og_partition(n, off[n], off, cols, w, cA, cB, -1.0, tol, seed, part, &res, NULL);
+  if (rc != OG_OK) goto done;
+  (*count)++;
+  if (!res.feasible) *feasible = 0;
+  newid = (int32_t*)malloc(nn * sizeof(int32_t));
+  soff = (int64_t*)malloc((nn + 1) * sizeof(int64_t));
+  scols = (int32_t*)malloc((size_t)(off[n] > 0 ? off[n] : 1) * sizeof(int32_t));
+  sw = (int32_t*)malloc((size_t)(off[n] > 0 ? off[n] : 1) * sizeof(int32_t));
+  sorig = (int32_t*)malloc(nn * sizeof(int32_t));
+  rc = OG_ERR_OOM;
+  if (!newid || !soff || !scols || !sw || !sorig) goto done;
+  for (int side = 0; side < 2; side++) {
+    int64_t sn = 0;
+    for (int64_t v = 0; v < n; v++) newid[v] = part[v] == side ? (int32_t)sn++ : -1;
+    int64_t se = 0;
+    soff[0] = 0;
+    for (int64_t v = 0; v < n; v++) {
+      if (part[v] != side) continue;
+      sorig[newid[v]] = orig[v];
+      for (int64_t e = off[v]; e < off[v + 1]; e++)
+        if (part[cols[e]] == side) {
+          scols[se] = newid[cols[e]];
+          sw[se] = w[e];
+          se++;
+        }
+      soff[newid[v] + 1] = se;
+    }
+    rc = og_bisect(sn, soff, scols, sw, n_all, costs, sorig, side ? mid : lo, side ? hi : mid, tol, seed, cls,
+                   feasible, count);
+    if (rc != OG_OK) goto done;
+  }
+  rc = OG_OK;
+done:
+  free(cA);
+  free(cB);
+  free(part);
+  free(newid);
+  free(soff);
+  free(scols);
+  free(sw);
+  free(sorig);
+  return rc;
+}
+
+int og_partition_kway(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                      int32_t k, const int32_t* costs, double tol, uint64_t seed, uint8_t* cls, int64_t* cut,
+                      int64_t* loads, int32_t* feasible, int32_t* bisections) {
+  if (k < 1 || k > 255) return OG_ERR_INVALID;
+  for (int32_t i = 0; i < k; i++) {
+    const int st = og_validate(n, m, off, cols, w, costs + (int64_t)i * n, costs + (int64_t)i * n);
+    if (st != OG_OK) return st;
+  }
+  int32_t* orig = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+  if (!orig) return OG_ERR_OOM;
+  for (int64_t v = 0; v < n; v++) orig[v] = (int32_t)v;
+  *feasible = 1;
+  *bisections = 0;
+  const int rc = og_bisect(n, off, cols, w, n, costs, orig, 0, k, tol, seed, cls, feasible, bisections);
+  free(orig);
+  if (rc != OG_OK) return rc;
+  int64_t c = 0;
+  for (int64_t u = 0; u < n; u++)
+    for (int64_t e = off[u]; e < off[u + 1]; e++)
+      if (cls[u] != cls[cols[e]]) c += w[e];
+  *cut = c;
+  for (int32_t i = 0; i < k; i++) loads[i] = 0;
+  for (int64_t v = 0; v < n; v++) loads[cls[v]] += costs[(int64_t)cls[v] * n + v];
+  return OG_OK;
+}

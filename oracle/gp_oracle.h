@@ -148,6 +148,17 @@ int og_partition_vcycle(int64_t n, int64_t m, const int64_t* off, const int32_t*
                         double r_cpu, double tol, uint64_t seed, uint8_t* part, og_result* res,
                         og_trace* trace);
 
+/* k device classes (1 <= k <= 255) by recursive bisection (Sec. VI's future third processor kind; the
+ * project's reading): costs[i * n + v] = v's time on class i; a group of classes acts as one device
+ * whose time for v folds its classes' times with floor(x*y / (x+y)); bisect(V', [lo, hi)) splits the
+ * subgraph induced by V' with og_partition (cpu_cost = group [lo, mid) with mid = lo + ceil((hi-lo)/2),
+ * gpu_cost = group [mid, hi), Eq. (1) bounds from their sums, tol, seed) and recurses on both sides.
+ * cls[v] in [0, k); cut over directed entries with different classes; loads[k]; feasible = every
+ * bisection feasible; bisections = how many ran. */
+int og_partition_kway(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
+                      int32_t k, const int32_t* costs, double tol, uint64_t seed, uint8_t* cls, int64_t* cut,
+                      int64_t* loads, int32_t* feasible, int32_t* bisections);
+
 int og_levels(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, int32_t* level,
               int32_t* nlevels);
 

@@ -65,6 +65,11 @@ MUTATIONS = {
                                  "                      lv[l].fix, BC, BG, pc, &rs) != OG_OK)"),
     "vcycle_coarsest_all_gpu": ("for (int64_t x = 0; x < lv[L].n; x++) pc[x] = (uint8_t)lv[L].fix[x];",
                                 "for (int64_t x = 0; x < lv[L].n; x++) pc[x] = 1;"),
+    "kway_group_time_summed": ("  return (int64_t)(((__int128)x * (__int128)y) / (__int128)(x + y));", "  return x + y;"),
+    "kway_mid_rounded_down": ("const int mid = lo + (hi - lo + 1) / 2;", "const int mid = lo + (hi - lo) / 2;"),
+    "kway_sides_swapped": ("rc = og_bisect(sn, soff, scols, sw, n_all, costs, sorig, side ? mid : lo, side ? hi : mid, tol, seed, cls,",
+                           "rc = og_bisect(sn, soff, scols, sw, n_all, costs, sorig, side ? lo : mid, side ? mid : hi, tol, seed, cls,"),
+    "kway_subgraph_loses_edges": ("        if (part[cols[e]] == side) {", "        if (0) {"),
     "no_twohop_in_pipeline": ("        og_match_twohop_fix(f->n, f->off, f->adj, f->W, f->vC, f->vG, f->fix, capC, capG, seed,\n"
                               "                            mate) != OG_OK) {", "        0) {"),
 }

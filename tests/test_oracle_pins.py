@@ -769,3 +769,107 @@ def test_vcycle_coarsens_through_levels_and_reports_them(oracle_mod):
     assert tr["n"][0] == g["n"] and res["coarsest_n"] == tr["n"][-1]
     assert all(a > b for a, b in zip(tr["n"], tr["n"][1:]))
     assert sum(tr["rounds"]) == res["rounds"]
+
+
+# ---------------------------------------------------------------------------
+# k device classes by recursive bisection
+# ---------------------------------------------------------------------------
+
+def _comb(*xs):
+    """Group time of classes working on one task together: 1/t = sum 1/t_i, floored pairwise."""
+    a = int(xs[0])
+    for b in xs[1:]:
+        b = int(b)
+        a = 0 if a + b == 0 else (a * b) // (a + b)
+    return a
+
+
+def _induced(g, keep):
+    """The subgraph on the vertices with keep[v] (renumbered in increasing id), every entry with both
+    ends kept; costs are left to the caller."""
+    ids = np.flatnonzero(keep)
+    new = -np.ones(g["n"], np.int64)
+    new[ids] = np.arange(ids.size)
+    edges, w = [], []
+    for u in ids:
+        for e in range(g["offsets"][u], g["offsets"][u + 1]):
+            v = int(g["cols"][e])
+            if keep[v]:
+                edges.append((int(new[u]), int(new[v])))
+                w.append(int(g["edge_cost"][e]))
+    return ids, edges, w
+
+
+def _costs3(g, seed):
+    rng = np.random.default_rng(seed)
+    fpga = np.maximum(0, (g["cpu_cost"].astype(np.int64) * rng.uniform(0.2, 0.8, g["n"]))).astype(np.int32)
+    return np.stack([g["cpu_cost"], g["gpu_cost"], fpga]).astype(np.int32)
+
+
+def test_kway_two_classes_is_the_2way_partition(oracle_mod):
+    for seed, g in enumerate([gen.cholesky(16), gen.lu(10), gen.layered(40, 150, 40000, 7)]):
+        cls, r = oracle_mod.partition_kway(g, np.stack([g["cpu_cost"], g["gpu_cost"]]), seed=seed)
+        part, res = oracle_mod.partition(g, seed=seed)
+        assert np.array_equal(cls, part) and r["cut"] == res["cut"]
+        assert r["loads"] == [res["load_cpu"], res["load_gpu"]] and r["feasible"] == res["feasible"]
+        assert r["bisections"] == 1
+
+
+def test_kway_one_class_takes_everything(oracle_mod):
+    g = gen.cholesky(8)
+    cls, r = oracle_mod.partition_kway(g, g["cpu_cost"][None, :])
+    assert not cls.any() and r == dict(cut=0, loads=[int(g["cpu_cost"].sum())], feasible=1, bisections=0)
+
+
+def test_kway_group_times_and_recursion(oracle_mod):
+    """k = 3: the first split is the 2-way problem between group {0, 1} (times folded as
+    floor(x*y/(x+y))) and class 2; then the {0, 1} side's induced subgraph is split between classes
+    0 and 1.  k = 4: groups {0, 1} and {2, 3} first, each then split on its own induced subgraph."""
+    for seed, g in enumerate([gen.lu(12), gen.layered(30, 120, 20000, 5), gen.random_dag(900, 4000, 2)]):
+        cs = _costs3(g, seed)
+        cls, r = oracle_mod.partition_kway(g, cs, seed=seed)
+        n = g["n"]
+        top = dict(g, cpu_cost=np.array([_comb(cs[0, v], cs[1, v]) for v in range(n)], np.int32),
+                   gpu_cost=cs[2].copy())
+        p1, _ = oracle_mod.partition(top, seed=seed)
+        assert np.array_equal(cls == 2, p1 == 1)
+        ids, edges, w = _induced(g, p1 == 0)
+        sub = gen.from_edges(ids.size, edges, cs[0, ids].tolist(), cs[1, ids].tolist(), w)
+        p2, _ = oracle_mod.partition(sub, seed=seed)
+        assert np.array_equal(cls[ids], p2)
+        # k = 4 (a second FPGA-like class)
+        cs4 = np.concatenate([cs, (cs[2:3] * 3 // 2).astype(np.int32)])
+        cls4, r4 = oracle_mod.partition_kway(g, cs4, seed=seed)
+        top4 = dict(g, cpu_cost=np.array([_comb(cs4[0, v], cs4[1, v]) for v in range(n)], np.int32),
+                    gpu_cost=np.array([_comb(cs4[2, v], cs4[3, v]) for v in range(n)], np.int32))
+        q, _ = oracle_mod.partition(top4, seed=seed)
+        assert np.array_equal(cls4 >= 2, q == 1)
+        for side, (a, b) in ((0, (0, 1)), (1, (2, 3))):
+            ids, edges, w = _induced(g, q == side)
+            if ids.size:
+                sub = gen.from_edges(ids.size, edges, cs4[a, ids].tolist(), cs4[b, ids].tolist(), w)
+                ps, _ = oracle_mod.partition(sub, seed=seed)
+                assert np.array_equal(cls4[ids], np.where(ps == 0, a, b))
+
+
+def test_kway_reported_cut_and_loads(oracle_mod):
+    for seed in range(6):
+        g = gen.random_dag(400, 2000, seed)
+        cs = _costs3(g, seed)
+        cls, r = oracle_mod.partition_kway(g, cs, seed=seed)
+        assert cls.max() < 3
+        cut = sum(int(g["edge_cost"][e]) for u in range(g["n"]) for e in range(g["offsets"][u], g["offsets"][u + 1])
+                  if cls[u] != cls[g["cols"][e]])
+        assert r["cut"] == cut
+        assert r["loads"] == [int(cs[i][cls == i].sum()) for i in range(3)]
+        assert r["bisections"] == 2
+
+
+def test_kway_rejects_bad_arguments(oracle_mod):
+    g = gen.cholesky(4)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.partition_kway(g, np.zeros((0, g["n"]), np.int32))
+    bad = np.stack([g["cpu_cost"], g["gpu_cost"]]).astype(np.int32)
+    bad[1, 3] = -1
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.partition_kway(g, bad)
