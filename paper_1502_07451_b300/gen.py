@@ -240,6 +240,29 @@ def _lognormal_costs(n: int, seed: int, mu: float, sigma: float, ratio_lo: float
     return cpu, gpu
 
 
+def _first_distinct(keys: np.ndarray, m: int):
+    """The first m distinct values of `keys` in draw order (a later repeat of a value is skipped),
+    sorted; (None, number of distinct values) if there are fewer than m.  Found with one plain sort
+    of all keys (repeats are rare) and a stable sort of the repeated values' occurrences only."""
+    s = np.sort(keys)
+    rep = s[1:] == s[:-1]
+    distinct = int(keys.shape[0] - np.count_nonzero(rep))
+    if distinct < m:
+        return None, distinct
+    if not rep.any():
+        return np.sort(keys[:m]), distinct
+    dup_vals = np.unique(s[1:][rep])
+    pos = np.minimum(np.searchsorted(dup_vals, keys), dup_vals.shape[0] - 1)
+    occ = np.flatnonzero(dup_vals[pos] == keys)  # every occurrence of a repeated value, in draw order
+    order = np.argsort(keys[occ], kind="stable")
+    ko = keys[occ][order]
+    later = np.concatenate([[False], ko[1:] == ko[:-1]])  # not the value's first occurrence
+    valid = np.ones(keys.shape[0], dtype=bool)
+    valid[occ[order][later]] = False
+    keep = np.flatnonzero(valid)[:m]
+    return np.sort(keys[keep]), distinct
+
+
 def layered(layers: int, width: int, m: int, seed: int, span: int = 4, wmax: int = 10000,
             mu: float = 10.0, sigma: float = 1.0, ratio_lo: float = 2.0, ratio_hi: float = 40.0):
     """Layered random DAG: ``layers`` x ``width`` vertices, ``m`` distinct edges.
@@ -275,12 +298,10 @@ def layered(layers: int, width: int, m: int, seed: int, span: int = 4, wmax: int
         lt = ls + 1 + (r1 % maxspan).astype(np.int64)
         dst = lt * width + (r2 % np.uint64(width)).astype(np.int64)
         keys = np.concatenate([keys, src * n + dst])
-        uniq, first = np.unique(keys, return_index=True)
-        if uniq.shape[0] >= m:
-            keep = np.sort(first)[:m]
-            sel = np.sort(keys[keep])
+        sel, distinct = _first_distinct(keys, m)
+        if sel is not None:
             break
-        need = m - uniq.shape[0]
+        need = m - distinct
     src = sel // n
     dst = (sel % n).astype(np.int32)
     counts = np.bincount(src, minlength=n).astype(np.int64)
