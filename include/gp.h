@@ -200,6 +200,30 @@ GP_API gp_status gp_makespan(const gp_graph* g, const uint8_t* part, int64_t* ma
                       void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * gp_partition_kway -- k device classes (1 <= k <= 255) by recursive bisection on the 2-way path.
+ * The paper names a third processor kind (an FPGA) as future work (Sec. VI) without its costs or a
+ * k-class Eq. (1)-(2); this library's reading: every task has one time per class; a group of classes
+ * acts as one device whose time for a task folds its classes' times with floor(x*y / (x+y)), left to
+ * right; the classes [lo, hi) split into [lo, mid) and [mid, hi), mid = lo + ceil((hi - lo) / 2),
+ * by gp_partition on the subgraph induced by the current vertices (group times as its CPU and GPU
+ * costs, Eq. (1) bounds from their sums, `tol`, `seed`), recursively; k = 2 is gp_partition.
+ *   n, m, offsets, cols, edge_cost   the DAG as in gp_graph_create (ptr_kind: 0 host, 1 device)
+ *   costs        int32[k * n], class-major: costs[i * n + v] = v's time on class i (>= 0)
+ *   cls_out      uint8[n] (device or host): the class of every vertex
+ *   cut          host int64: sum of edge_cost over edges whose ends have different classes
+ *   loads        host int64[k]: sum of costs[i * n + v] over the vertices of class i
+ *   feasible     host int32 or NULL: 1 if every bisection met its bounds
+ *   bisections   host int32 or NULL: bisections run (k - 1 unless a side came out empty)
+ * Errors (in this precedence): GP_ERR_INVALID (k, sizes, tol, a negative time, the CSR),
+ * GP_ERR_OVERFLOW (a class's or the transfers' sum above 2^61), GP_ERR_NOT_DAG, GP_ERR_OOM,
+ * GP_ERR_CUDA, GP_ERR_TIMEOUT.
+ * ------------------------------------------------------------------------------------------- */
+GP_API gp_status gp_partition_kway(int64_t n, int64_t m, const int64_t* offsets, const int32_t* cols,
+                                   const int32_t* edge_cost, int32_t k, const int32_t* costs, int ptr_kind,
+                                   double tol, uint64_t seed, uint8_t* cls_out, int64_t* cut, int64_t* loads,
+                                   int32_t* feasible, int32_t* bisections, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * gp_makespan_workers -- makespan of a mapping on a fixed number of workers per side.  The paper's
  * testbed runs the kernels on 3 CPU worker cores and 1 GPU worker (Sec. IV.A); gp_makespan assumes as
  * many workers as a level needs.  Here every task runs without preemption on one worker of its side

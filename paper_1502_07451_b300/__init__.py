@@ -89,6 +89,9 @@ def lib():
                 "gp_makespan": [_P, _P, _P, _P, _P],
                 "gp_cut": [_P, _P, _P, _P],
                 "gp_makespan_noalloc": [_P, _P, _P, _P, _P],
+                "gp_makespan_workers": [_P, _P, _I32, _I32, _P, _P, _P],
+                "gp_partition_kway": [_I64, _I64, _P, _P, _P, _I32, _P, C.c_int, _D, _U64, _P, _P, _P, _P, _P, _P],
+                "gp_batch_makespan_workers": [_I32, _P, _P, _I32, _I32, _P, _P],
                 "gp_step_match": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _I32, _I32, _P, _P],
                 "gp_step_contract": [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
                 "gp_step_gggp": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _P, _P, _P],
@@ -111,6 +114,7 @@ def lib():
                 "gp_model_grad": [_P, _P, _P, _P, _P, _P],
                 "gp_model_train_step": [_P, _P, _P, C.c_float, _P, _P],
                 "gp_partition_learned": [_P, _P, _P, _D, _D, _P, _P, _P],
+                "gp_partition_learned_vcycle": [_P, _P, _P, _D, _D, _U64, _P, _P, _P],
                 "gp_batch_partition_learned": [_I32, _P, _P, _P, _D, _P, _P, _P, _P],
                 "gp_graph_create_batch": [_I32, _P, _P, _P, _P, _P, _P, _P, C.c_int, _P, _P, _P],
                 "gp_selftest_wait_timeout": [_I32, _P],
@@ -285,16 +289,60 @@ def gp_makespan(h, part, finish_out=None, stream=None):
     return int(ms.value)
 
 
+def gp_partition_kway(g, costs, cls_out, tol=0.03, seed=0, stream=None):
+    """k device classes by recursive bisection.  g: dict with n, m, offsets, cols, edge_cost (all host
+    or all device); costs: int32 [k, n] (same memory kind); cls_out: uint8[n] (device or host).
+    Returns dict(cut, loads (list of k), feasible, bisections)."""
+    n, m = int(g["n"]), int(g["m"])
+    k = int(costs.shape[0])
+    ptrs = [_ptr(g[key]) for key in ("offsets", "cols", "edge_cost")] + [_ptr(costs)]
+    kinds = {p[1] for p in ptrs if p[0]}
+    if len(kinds) > 1:
+        raise ValueError("CSR arrays and costs must all be host or all be device memory")
+    kind = kinds.pop() if kinds else 0
+    cut = C.c_int64()
+    loads = (C.c_int64 * max(k, 1))()
+    feas = C.c_int32()
+    nb = C.c_int32()
+    _check(lib().gp_partition_kway(n, m, ptrs[0][0], ptrs[1][0], ptrs[2][0], k, ptrs[3][0], kind, float(tol), int(seed),
+                                   _ptr(cls_out)[0], C.byref(cut), loads, C.byref(feas), C.byref(nb), _stream(stream)),
+           "gp_partition_kway")
+    return dict(cut=int(cut.value), loads=[int(loads[i]) for i in range(k)], feasible=int(feas.value),
+                bisections=int(nb.value))
+
+
+def gp_makespan_workers(h, part, workers_cpu=3, workers_gpu=1, finish_out=None, stream=None):
+    """Makespan of the mapping on a fixed number of workers per side (a list schedule; the paper's
+    testbed has 3 CPU workers and 1 GPU worker)."""
+    ms = C.c_int64()
+    _check(lib().gp_makespan_workers(h, _ptr(part)[0], int(workers_cpu), int(workers_gpu), C.byref(ms),
+                                     _ptr(finish_out)[0], _stream(stream)), "gp_makespan_workers")
+    return int(ms.value)
+
+
+def gp_batch_makespan_workers(handles, parts, workers_cpu=3, workers_gpu=1, stream=None):
+    """gp_makespan_workers for many graphs in one launch; returns the makespans (list)."""
+    count, hs, _, _ = _batch_args(handles, None, None)
+    if len(parts) != count:
+        raise ValueError("one split buffer per graph")
+    pp = (_P * max(count, 1))(*[_ptr(p)[0] for p in parts])
+    ms = (C.c_int64 * max(count, 1))()
+    _check(lib().gp_batch_makespan_workers(count, hs, pp, int(workers_cpu), int(workers_gpu), ms, _stream(stream)),
+           "gp_batch_makespan_workers")
+    return [int(ms[i]) for i in range(count)]
+
+
 MAKESPAN_NOALLOC_MAX_N = 1 << 20
 
 
 def gp_makespan_noalloc(h, part, finish_out=None, stream=None):
     """gp_makespan without any device allocation (scratch compiled into the library).
 
-    For callers that cannot allocate device memory.  ``part`` and ``finish_out`` must be device
-    tensors; at most MAKESPAN_NOALLOC_MAX_N vertices; calls that overlap on one GPU race on the
-    shared scratch.  The first call on a device resolves the scratch address: make it before any
-    stream capture.
+    For callers that cannot allocate device memory (a host allocator that owns all of it, a
+    latency-critical loop).  ``part`` and ``finish_out`` must be device tensors; at most
+    MAKESPAN_NOALLOC_MAX_N vertices; the call synchronises ``stream``; calls that overlap on one
+    GPU race on the shared scratch.  The first call on a device (and the first after a reset of
+    its context) resolves the scratch address: make it before any stream capture.
     """
     ms = C.c_int64()
     st = lib().gp_makespan_noalloc(h, _ptr(part)[0], C.byref(ms), _ptr(finish_out)[0], _stream(stream))
@@ -484,6 +532,16 @@ def gp_partition_learned(g, model, part_out, logits=None, r_cpu=-1.0, tol=0.03, 
     res = Result()
     _check(lib().gp_partition_learned(g, model, _ptr(logits)[0], float(r_cpu), float(tol), _ptr(part_out)[0],
                                       C.byref(res), _stream(stream)), "gp_partition_learned")
+    return res.as_dict()
+
+
+def gp_partition_learned_vcycle(g, model, part_out, logits=None, r_cpu=-1.0, tol=0.03, seed=0, stream=None):
+    """The learned path as a V-cycle: the proposal restricts the matching to same-side pairs, the
+    coarsest split is the proposed sides, and every level is refined on the way back."""
+    res = Result()
+    _check(lib().gp_partition_learned_vcycle(g, model, _ptr(logits)[0], float(r_cpu), float(tol), int(seed),
+                                             _ptr(part_out)[0], C.byref(res), _stream(stream)),
+           "gp_partition_learned_vcycle")
     return res.as_dict()
 
 

@@ -24,12 +24,13 @@
 #include "k_mpnn.cuh"
 #include "k_propose.cuh"
 #include "k_create.cuh"
+#include "k_listsched.cuh"
 
 namespace gp {
 
 const char* const kFamilyName[F_COUNT] = {
     "validate", "transpose", "levels", "sym_merge", "match_pick", "match_confirm", "twohop", "cmap",
-    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch", "mpnn", "propose", "refine"};
+    "contract_merge", "scan", "gggp", "gain", "select", "apply", "project", "makespan", "cut", "misc", "batch", "mpnn", "propose", "refine", "listsched"};
 
 // ------------------------------------------------------------------------------------------------
 // launch accounting and optional per-launch event timing
@@ -847,8 +848,21 @@ struct TraceDev {
   int32_t tail_err;   // a grid refinement barrier wait expired
 };
 
+// Coarse split of the V-cycle: every coarse vertex holds members of one proposed side (its pin).
+__global__ void k_pins_to_part(int64_t n, const int8_t* __restrict__ pin, uint8_t* __restrict__ part,
+                               int32_t* trial) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    part[i] = (uint8_t)pin[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *trial = -1;
+}
+
+// The multilevel bipartitioner.  fixed: NULL, or one pin per vertex (host or device; -1 free, 0 CPU,
+// 1 GPU).  restrict_only = false: the pins hold through every step (gp_partition_fixed).
+// restrict_only = true (the learned V-cycle, every vertex pinned to its proposed side): the pins only
+// keep the matching to same-side pairs; the coarsest level's split is its pins and refinement moves
+// any vertex.
 static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
-                                uint8_t* part_out, gp_result* res, void* stream) {
+                                uint8_t* part_out, gp_result* res, void* stream, bool restrict_only = false) {
   if (!g || (!part_out && g->n > 0)) return GP_ERR_INVALID;
   int64_t BC, BG;
   gp_status st = host_bounds(g->SC, g->SG, r_cpu, tol, &BC, &BG);
@@ -960,7 +974,15 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
     if (prof) cudaEventRecord(ev[1], s);
     std::vector<uint8_t*> parts(Lc + 1, nullptr);
     parts[Lc] = A.get<uint8_t>(L[Lc].n);
-    gggp(L[Lc], BC, BG, g->SG, seed, parts[Lc], &td->trial, s);
+    if (restrict_only) {
+      // the coarsest split is the proposed sides; from here on no vertex is pinned
+      GP_LAUNCH(F_GGGP, k_pins_to_part, grid_for(L[Lc].n, 256), 256, 0, s, L[Lc].n, (const int8_t*)L[Lc].fix,
+                parts[Lc], &td->trial);
+      GP_CHECK_LAUNCH();
+      for (auto& lg : L) lg.fix = nullptr;
+    } else {
+      gggp(L[Lc], BC, BG, g->SG, seed, parts[Lc], &td->trial, s);
+    }
     if (prof) cudaEventRecord(ev[2], s);
     Ctl hctl;
     memset(&hctl, 0, sizeof(hctl));
@@ -1376,6 +1398,10 @@ gp_status gp_step_refine(int64_t n, const int64_t* off, const int32_t* adj, cons
 
 // the no-allocation makespan variant (its scratch array must share this translation unit)
 #include "gp_noalloc.cu"
+
+#include "gp_listsched.cu"
+
+#include "gp_kway.cu"
 // many graphs in one persistent launch
 #include "gp_batch.cu"
 // the learned proposal (message-passing network on the tensor cores)

@@ -29,7 +29,7 @@ constexpr int64_t kMaxN = (int64_t(1) << 31) - 2;
 enum Family {
   F_VALIDATE = 0, F_TRANSPOSE, F_LEVELS, F_SYM_MERGE, F_MATCH_PICK, F_MATCH_CONFIRM, F_TWOHOP,
   F_CMAP, F_CONTRACT_MERGE, F_SCAN, F_GGGP, F_GAIN, F_SELECT, F_APPLY, F_PROJECT, F_MAKESPAN,
-  F_CUT, F_MISC, F_BATCH, F_MPNN, F_PROPOSE, F_REFINE, F_COUNT
+  F_CUT, F_MISC, F_BATCH, F_MPNN, F_PROPOSE, F_REFINE, F_LISTSCHED, F_COUNT
 };
 extern const char* const kFamilyName[F_COUNT];
 

@@ -662,6 +662,64 @@ gp_status gp_partition_learned(gp_graph* g, const gp_model* M, const float* logi
   }
 }
 
+gp_status gp_partition_learned_vcycle(gp_graph* g, const gp_model* M, const float* logits, double r_cpu,
+                                      double tol, uint64_t seed, uint8_t* part_out, gp_result* res, void* stream) {
+  if (!g || (!M && !logits) || (!part_out && g->n > 0)) return GP_ERR_INVALID;
+  if (M) {
+    gp_status st = mp_check(M, g);
+    if (st != GP_OK) return st;
+  }
+  int64_t BC, BG;
+  gp_status st = host_bounds(g->SC, g->SG, r_cpu, tol, &BC, &BG);
+  if (st != GP_OK) return st;
+  const int64_t n = g->n;
+  if (n == 0) return partition_impl(g, nullptr, r_cpu, tol, seed, part_out, res, stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    pool_setup();
+    Arena A(s);
+    const bool prof = prof_on();
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (prof) {
+      for (auto& e : ev) cudaEventCreate(&e);
+      cudaEventRecord(ev[0], s);
+    }
+    float* lg = A.get<float>(n);
+    int herr = 0;
+    if (logits) {
+      GP_CUDA(cudaMemcpyAsync(lg, logits, sizeof(float) * n, cudaMemcpyDefault, s));
+    } else {
+      MpWork W;
+      mp_prepare(g, s);
+      const MpGraph G = mp_graph(g);
+      mp_work(W, G, false, A, s);
+      mp_forward(M, G, W, nullptr, false, s);
+      GP_CUDA(cudaMemcpyAsync(lg, W.logit, sizeof(float) * n, cudaMemcpyDeviceToDevice, s));
+      GP_CUDA(cudaMemcpyAsync(&herr, W.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    }
+    uint8_t* prop = A.get<uint8_t>(n);
+    propose_split(g, lg, BC, BG, prop, A, s);  // synchronises
+    if (herr) return GP_ERR_TIMEOUT;
+    float net_ms = 0.0f;
+    if (prof) {
+      cudaEventRecord(ev[1], s);
+      cudaEventSynchronize(ev[1]);
+      cudaEventElapsedTime(&net_ms, ev[0], ev[1]);
+      for (auto& e : ev) cudaEventDestroy(e);
+    }
+    // the proposed sides (0 / 1) pin every vertex for the matching only
+    gp_result R;
+    st = partition_impl(g, (const int8_t*)prop, r_cpu, tol, seed, part_out, &R, stream, true);
+    if (st != GP_OK) return st;
+    R.ms[4] = net_ms;
+    if (res) *res = R;
+    return GP_OK;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------------

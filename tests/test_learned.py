@@ -247,3 +247,61 @@ def test_network_is_deterministic_across_handles():
         a = gpu_logits(M, G1, g["n"])
         b = gpu_logits(M, G2, g["n"])
     assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# The learned path as a V-cycle (restricted coarsening, refinement at every level)
+# ---------------------------------------------------------------------------
+
+TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1502_07451_b300",
+                       "models", "mpnn3_h64.bin")
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS) + ["layered_big", "cholesky24", "lu16"])
+def test_vcycle_matches_oracle_given_logits(name):
+    """Split, every result field and the per-level trace equal the oracle's V-cycle run on the
+    network's logits (the trained checkpoint), for the network's own logits and passed-in ones."""
+    extra = {"layered_big": lambda: gen.layered(200, 500, 400000, 12), "cholesky24": lambda: gen.cholesky(24),
+             "lu16": lambda: gen.lu(16)}
+    g = GRAPHS[name]() if name in GRAPHS else extra[name]()
+    n = g["n"]
+    model = gp.gp_model_load(TRAINED)
+    try:
+        with gp.Graph(dgraph(g)) as G:
+            logits = torch.empty(n, dtype=torch.float32, device="cuda")
+            gp.gp_model_forward(model, G.h, logits)
+            part = torch.empty(n, dtype=torch.uint8, device="cuda")
+            res = gp.gp_partition_learned_vcycle(G.h, model, part, seed=3)
+            tr = G.trace()
+            part2 = np.zeros(n, np.uint8)
+            res2 = gp.gp_partition_learned_vcycle(G.h, None, part2, logits=logits.cpu().numpy(), seed=3)
+    finally:
+        gp.gp_model_destroy(model)
+    ref_part, ref, otr = oracle.partition_vcycle(g, logits.cpu().numpy(), seed=3, trace=True)
+    assert np.array_equal(part.cpu().numpy(), ref_part)
+    assert np.array_equal(part2, ref_part)
+    for k in KEYS:
+        assert res[k] == ref[k] and res2[k] == ref[k], k
+    assert tr["n"] == otr["n"] and tr["a"] == otr["a"] and tr["rounds"] == otr["rounds"]
+    assert tr["gggp_trial"] == -1
+
+
+def test_vcycle_ratio_branches_and_noisy_logits():
+    g = gen.layered(60, 300, 120000, 3)
+    n = g["n"]
+    p0, _ = oracle.partition(g)
+    rng = np.random.default_rng(4)
+    lg = (np.where(p0 == 0, 1.0, -1.0) + rng.normal(0, 0.8, n)).astype(np.float32)
+    with gp.Graph(dgraph(g)) as G:
+        for r in (-1.0, 0.0, 0.2, 1.0):
+            part = torch.empty(n, dtype=torch.uint8, device="cuda")
+            res = gp.gp_partition_learned_vcycle(G.h, None, part, logits=torch.from_numpy(lg).cuda(), r_cpu=r)
+            ref_part, ref = oracle.partition_vcycle(g, lg, r_cpu=r)
+            assert np.array_equal(part.cpu().numpy(), ref_part), r
+            assert all(res[k] == ref[k] for k in KEYS), r
+        bad = lg.copy()
+        bad[7] = np.nan
+        with pytest.raises(gp.GpError) as e:
+            gp.gp_partition_learned_vcycle(G.h, None, torch.empty(n, dtype=torch.uint8, device="cuda"),
+                                           logits=torch.from_numpy(bad).cuda())
+        assert e.value.status == gp.GP_ERR_INVALID
