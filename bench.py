@@ -630,6 +630,7 @@ def run_layered_line(args, rank, world, local_rank):
         bit_exact = golden_16m_match(M["part"], M["res"], M["makespan"])
 
     fixed = bench_fixed(g1, K, W, stream, flush, with_oracle=with_oracle)
+    kway = bench_kway(g1, 3, K, W, stream, flush, with_oracle=with_oracle)
     learned = learned16 = None
     if not args.no_learned:
         learned = bench_learned(g1, one_m["part_dev"], one_m["res"], one_m["makespan"], K, W, stream, flush,
@@ -700,6 +701,8 @@ def run_layered_line(args, rank, world, local_rank):
         line["learned_16m"] = learned16
     if fixed:
         line["fixed"] = fixed
+    if kway:
+        line["kway"] = kway
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -761,6 +764,44 @@ def bench_fixed(g, K, W, stream, flush, with_oracle):
         opart, ores = oracle.partition(hs, fixed=fx)
         out["bit_exact_vs_oracle"] = bool(np.array_equal(opart, p) and ores["cut"] == res["cut"]
                                           and ores["load_cpu"] == res["load_cpu"])
+    return out
+
+
+def bench_kway(g, k, K, W, stream, flush, with_oracle):
+    """k device classes by recursive bisection (gp_partition_kway) on the workload: CPU, GPU and an
+    FPGA-like class (gen.kway_costs), device-resident inputs; K steps after W warm-ups, L2 flushed
+    between steps; checked against the oracle in the CPU-baseline leg."""
+    import torch
+    import paper_1502_07451_b300 as gp
+    from paper_1502_07451_b300 import gen
+    cs = gen.kway_costs(g, k, 0)
+    d = {key: torch.from_numpy(g[key]).cuda() for key in ("offsets", "cols", "edge_cost")}
+    d.update(n=g["n"], m=g["m"])
+    dcs = torch.from_numpy(cs).cuda()
+    cls = torch.empty(g["n"], dtype=torch.uint8, device="cuda")
+    for _ in range(W):
+        r = gp.gp_partition_kway(d, dcs, cls, stream=stream)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(K):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = gp.gp_partition_kway(d, dcs, cls, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    out = {"entry": "gp_partition_kway", "classes": k,
+           "class_costs": "CPU, GPU, and an FPGA-like class: CPU time x U(0.1, 0.9) per task (gen.kway_costs)",
+           "metric": METRIC, "value": K * g["m"] / (tot / 1e3), "unit": UNIT, "ms_per_step": tot / K,
+           "cut": r["cut"], "loads": r["loads"], "feasible": r["feasible"], "bisections": r["bisections"],
+           "vertices_per_class": [int(x) for x in np.bincount(cls.cpu().numpy(), minlength=k)]}
+    if with_oracle:  # the CPU-baseline leg
+        import oracle
+        t0 = time.perf_counter()
+        ocls, orr = oracle.partition_kway(g, cs)
+        out["oracle_s"] = time.perf_counter() - t0
+        out["bit_exact_vs_oracle"] = bool(np.array_equal(ocls, cls.cpu().numpy()) and orr == r)
     return out
 
 

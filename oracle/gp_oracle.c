@@ -1485,11 +1485,19 @@ done:
 int og_partition_kway(int64_t n, int64_t m, const int64_t* off, const int32_t* cols, const int32_t* w,
                       int32_t k, const int32_t* costs, double tol, uint64_t seed, uint8_t* cls, int64_t* cut,
                       int64_t* loads, int32_t* feasible, int32_t* bisections) {
-  if (k < 1 || k > 255) return OG_ERR_INVALID;
+  /* checks in the precedence of og_validate: INVALID (arguments, any class's negative time, the
+   * CSR), then OVERFLOW (a class's or the transfers' sum above 2^61), then NOT_DAG */
+  if (k < 1 || k > 255 || n < 0 || !(tol >= 0.0 && tol <= 1.0)) return OG_ERR_INVALID;
+  for (int64_t i = 0; i < (int64_t)k * n; i++)
+    if (costs[i] < 0) return OG_ERR_INVALID;
+  const int st0 = og_validate(n, m, off, cols, w, costs, costs);
+  if (st0 == OG_ERR_INVALID) return st0;
   for (int32_t i = 0; i < k; i++) {
-    const int st = og_validate(n, m, off, cols, w, costs + (int64_t)i * n, costs + (int64_t)i * n);
-    if (st != OG_OK) return st;
+    int64_t s = 0;
+    for (int64_t v = 0; v < n; v++) s += costs[(int64_t)i * n + v];
+    if (s > OG_SUM_LIMIT) return OG_ERR_OVERFLOW;
   }
+  if (st0 != OG_OK) return st0;
   int32_t* orig = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
   if (!orig) return OG_ERR_OOM;
   for (int64_t v = 0; v < n; v++) orig[v] = (int32_t)v;

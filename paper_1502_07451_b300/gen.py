@@ -459,6 +459,20 @@ def config_layered_16m(seed: int = 0):
     return layered(1000, 16000, 128_000_000, seed)
 
 
+def kway_costs(g, k: int, seed: int = 0):
+    """Times of k device classes for the k-way split (int32 [k, n]): class 0 the CPU time, class 1 the
+    GPU time, and each further class an accelerator derived from them with per-task speed factors
+    (stream 50 + i): even classes CPU time x U(0.1, 0.9) (an FPGA-like part faster than the CPU on
+    every task), odd classes GPU time x U(0.5, 3.0), floored."""
+    n = g["n"]
+    out = [np.asarray(g["cpu_cost"], np.int64), np.asarray(g["gpu_cost"], np.int64)]
+    for i in range(2, k):
+        u = uniform(seed, 50 + i, 0, n)
+        f = 0.1 + 0.8 * u if i % 2 == 0 else 0.5 + 2.5 * u
+        out.append(np.floor(out[i % 2] * f).astype(np.int64))
+    return np.ascontiguousarray(np.stack(out[:k]).astype(np.int32))
+
+
 def nearest_T(target: int, tasks_fn, lo: int, hi: int) -> int:
     best = lo
     for T in range(lo, hi + 1):
