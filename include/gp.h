@@ -403,7 +403,11 @@ GP_API int64_t gp_model_param_count(void);
 /* FP32 parameters to / from host memory (GP_MPNN_PARAMS floats); set resets the optimiser. */
 GP_API gp_status gp_model_get_params(const gp_model* m, float* params);
 GP_API gp_status gp_model_set_params(gp_model* m, const float* params);
-/* Checkpoint: parameters, Adam moments and step (a private binary format with a magic header). */
+/* Checkpoint: parameters, Adam moments and step: magic "GPMPNN01", uint32 version (2), uint32 parameter
+ * count, int64 step, float32 parameters / first / second moments, uint64 FNV-1a checksum of the bytes
+ * between the magic and the checksum (all little-endian).  gp_model_load also reads version 1 (no
+ * checksum) and rejects a wrong checksum, a truncated or longer file, or a non-finite value with
+ * GP_ERR_INVALID. */
 GP_API gp_status gp_model_save(const gp_model* m, const char* path);
 GP_API gp_status gp_model_load(const char* path, gp_model** out);
 /* logits_out: float[n], device or host. */
@@ -457,6 +461,19 @@ GP_API gp_status gp_selftest_wait_timeout(int32_t limit_ms, void* stream);
  * arriving, so CTA 0's bounded wait (0.5 s) gives up.  Returns GP_ERR_TIMEOUT when it did (the context
  * stays usable), GP_ERR_CUDA if the device has no cooperative launch. */
 GP_API gp_status gp_selftest_grid_wait_timeout(void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Checked build.  libgp_checked.so is this library compiled with GP_CHECKED: every data-dependent index
+ * the kernels gather with (neighbour ids, match partners, coarse ids, successor ids) is tested against
+ * its range first; a failed test records its site number in a device word (the first one wins) and the
+ * access is skipped, so the results are then meaningless but no access leaves its array.
+ * gp_checked_site returns that site (0: none) and clears it when `clear` is nonzero; -1 in the
+ * unchecked build.  gp_selftest_checked runs one gather through an out-of-range index behind the test
+ * (site 99) and returns GP_OK when the gather was skipped; in the unchecked build it launches nothing
+ * and returns GP_ERR_INVALID.
+ * ------------------------------------------------------------------------------------------- */
+GP_API int32_t gp_checked_site(int32_t clear);
+GP_API gp_status gp_selftest_checked(void* stream);
 
 /* ---------------------------------------------------------------------------------------------
  * Instrumentation.

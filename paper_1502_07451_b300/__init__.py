@@ -74,7 +74,8 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build()
+            # GP_LIBRARY=checked loads the checked build (every gathered index tested in-kernel)
+            path = _build.build(checked=os.environ.get("GP_LIBRARY") == "checked")
             L = C.CDLL(path)
             sig = {
                 "gp_graph_create": [_I64, _I64, _P, _P, _P, _P, _P, C.c_int, _P, C.POINTER(_P)],
@@ -90,6 +91,7 @@ def lib():
                 "gp_cut": [_P, _P, _P, _P],
                 "gp_makespan_noalloc": [_P, _P, _P, _P, _P],
                 "gp_makespan_workers": [_P, _P, _I32, _I32, _P, _P, _P],
+                "gp_selftest_checked": [_P],
                 "gp_partition_kway": [_I64, _I64, _P, _P, _P, _I32, _P, C.c_int, _D, _U64, _P, _P, _P, _P, _P, _P],
                 "gp_batch_makespan_workers": [_I32, _P, _P, _I32, _I32, _P, _P],
                 "gp_step_match": [_I64, _P, _P, _P, _P, _P, _I64, _I64, _U64, _I32, _I32, _P, _P],
@@ -136,12 +138,15 @@ def lib():
             L.gp_batch_schedule_count.restype = C.c_int32
             L.gp_batch_schedule_name.argtypes = [_I32]
             L.gp_batch_schedule_name.restype = C.c_char_p
+            L.gp_checked_site.argtypes = [_I32]
+            L.gp_checked_site.restype = C.c_int32
             _lib = L
     return _lib
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library file lib() loads (libgp.so, or libgp_checked.so with GP_LIBRARY=checked)."""
+    return _build.LIB_CHECKED if os.environ.get("GP_LIBRARY") == "checked" else _build.LIB
 
 
 def status_string(st: int) -> str:
@@ -543,6 +548,17 @@ def gp_partition_learned_vcycle(g, model, part_out, logits=None, r_cpu=-1.0, tol
                                              _ptr(part_out)[0], C.byref(res), _stream(stream)),
            "gp_partition_learned_vcycle")
     return res.as_dict()
+
+
+def gp_checked_site(clear: bool = True) -> int:
+    """Checked build: the site of the first failed in-kernel index test since the last clear (0: none);
+    -1 in the unchecked build."""
+    return int(lib().gp_checked_site(1 if clear else 0))
+
+
+def gp_selftest_checked(stream=None):
+    """Checked build: one gather through an out-of-range index behind its test (site 99)."""
+    _check(lib().gp_selftest_checked(_stream(stream)), "gp_selftest_checked")
 
 
 def gp_launch_count() -> int:

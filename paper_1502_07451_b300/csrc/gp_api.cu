@@ -169,10 +169,18 @@ static void pool_setup() {
   g_pool_set[d] = true;
 }
 
+// Host-side fault injection for the error paths (nothing is done to the GPU): GP_FAULT=oom makes every
+// device allocation fail as out of memory, GP_FAULT=cuda as a failed runtime call, and GP_FAULT=timeout
+// makes the partition report an expired device wait after its kernels completed normally.
+static bool fault_is(const char* what) {
+  const char* f = getenv("GP_FAULT");
+  return f && strcmp(f, what) == 0;
+}
+
 void* dalloc(size_t bytes, cudaStream_t s) {
   void* p = nullptr;
-  const char* f = getenv("GP_FAULT");
-  if (f && strcmp(f, "oom") == 0) throw Fail{GP_ERR_OOM};
+  if (fault_is("oom")) throw Fail{GP_ERR_OOM};
+  if (fault_is("cuda")) throw Fail{GP_ERR_CUDA};
   GP_CUDA(cudaMallocAsync(&p, bytes ? bytes : 1, s));
   return p;
 }
@@ -1061,7 +1069,7 @@ static gp_status partition_impl(gp_graph* g, const int8_t* fixed, double r_cpu, 
     TraceDev h;
     GP_CUDA(cudaMemcpyAsync(&h, td, sizeof(TraceDev), cudaMemcpyDeviceToHost, s));
     GP_CUDA(cudaStreamSynchronize(s));
-    if (h.tail_err) throw Fail{GP_ERR_TIMEOUT};
+    if (h.tail_err || fault_is("timeout")) throw Fail{GP_ERR_TIMEOUT};
     R.cut = (int64_t)h.cut;
     R.load_cpu = h.ctl.LC;
     R.load_gpu = h.ctl.LG;
@@ -1100,6 +1108,59 @@ gp_status gp_partition(gp_graph* g, double r_cpu, double tol, uint64_t seed, uin
 gp_status gp_partition_fixed(gp_graph* g, const int8_t* fixed, double r_cpu, double tol, uint64_t seed,
                              uint8_t* part_out, gp_result* res, void* stream) {
   return partition_impl(g, fixed, r_cpu, tol, seed, part_out, res, stream);
+}
+
+// Checked build: the site of the first failed index test since the last clear (0: none); -1 without
+// GP_CHECKED.
+int32_t gp_checked_site(int32_t clear) {
+#ifdef GP_CHECKED
+  int site = 0;
+  if (cudaMemcpyFromSymbol(&site, d_check_site, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return -2;
+  }
+  if (clear) {
+    const int zero = 0;
+    if (cudaMemcpyToSymbol(d_check_site, &zero, sizeof(int)) != cudaSuccess) cudaGetLastError();
+  }
+  return site;
+#else
+  (void)clear;
+  return -1;
+#endif
+}
+
+#ifdef GP_CHECKED
+// One thread gathers through an index it tests first: idx is out of range, so the test records site 99
+// and the gather does not happen.
+__global__ void k_checked_selftest(const int32_t* __restrict__ a, int64_t n, int64_t idx, int32_t* out) {
+  int32_t v = -1;
+  if (GP_IN(idx, n, 99)) v = a[idx];
+  *out = v;
+}
+#endif
+
+gp_status gp_selftest_checked(void* stream) {
+#ifdef GP_CHECKED
+  cudaStream_t s = (cudaStream_t)stream;
+  try {
+    int32_t* buf = dnew<int32_t>(5, s);
+    GP_CUDA(cudaMemsetAsync(buf, 0, 5 * sizeof(int32_t), s));
+    GP_LAUNCH(F_MISC, k_checked_selftest, 1, 1, 0, s, (const int32_t*)buf, (int64_t)4, (int64_t)1000000, buf + 4);
+    GP_CHECK_LAUNCH();
+    int32_t v = 0;
+    GP_CUDA(cudaMemcpyAsync(&v, buf + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    GP_CUDA(cudaStreamSynchronize(s));
+    dfree(buf, s);
+    return v == -1 ? GP_OK : GP_ERR_CUDA;
+  } catch (Fail& f) {
+    cudaGetLastError();
+    return f.st;
+  }
+#else
+  (void)stream;
+  return GP_ERR_INVALID;  // the unchecked build has no test to skip the gather: nothing is launched
+#endif
 }
 
 gp_status gp_selftest_grid_wait_timeout(void* stream) {

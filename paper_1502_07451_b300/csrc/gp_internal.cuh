@@ -33,6 +33,25 @@ enum Family {
 };
 extern const char* const kFamilyName[F_COUNT];
 
+// ------------------------------------------------------------------------------------------------
+// Checked build (-DGP_CHECKED, libgp_checked.so): every data-dependent index the kernels gather with
+// (neighbour ids, match partners, coarse ids, level positions) is tested against its range before the
+// access; a failing test records the check's site number in a device word (the first one wins) and the
+// access is skipped, so a corrupt input turns into a recorded site instead of an out-of-range access.
+// Without GP_CHECKED the test is the constant `true` and compiles away.
+// ------------------------------------------------------------------------------------------------
+#ifdef GP_CHECKED
+__device__ int d_check_site;
+__device__ __forceinline__ bool gp_in_range(int64_t i, int64_t n, int site) {
+  if ((uint64_t)i < (uint64_t)n) return true;
+  atomicCAS(&d_check_site, 0, site);
+  return false;
+}
+#define GP_IN(i, n, site) ::gp::gp_in_range((int64_t)(i), (int64_t)(n), (site))
+#else
+#define GP_IN(i, n, site) true
+#endif
+
 // Device counters of algorithmic bytes per family (added by kernels, one atomic per block).  The
 // library is a single translation unit, so the definition lives here.
 __device__ unsigned long long d_alg_bytes[F_COUNT];
@@ -267,6 +286,7 @@ struct TwoSrc {
   const int32_t* row_b;    // source row of segment B (NULL: r); -1 = none
   const int32_t* map;      // column map (NULL: identity)
   int32_t drop_self;       // drop mapped column == r
+  int64_t map_n;           // entries of `map` (checked build: the ids it is indexed with; 0 = unknown)
 };
 // Writes deg_out[r] and the merged row at out_start[r] (capacity = raw length).
 // raw_bound >= total raw entries (sizes the scratch of the long-row tier).

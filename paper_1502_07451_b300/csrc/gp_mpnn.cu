@@ -416,6 +416,20 @@ gp_status gp_model_set_params(gp_model* M, const float* params) {
 
 static const char kModelMagic[8] = {'G', 'P', 'M', 'P', 'N', 'N', '0', '1'};
 
+// Checkpoint layout (little-endian): magic "GPMPNN01", uint32 version, uint32 parameter count, int64
+// Adam step, float32 parameters / first moments / second moments, and from version 2 on a uint64
+// FNV-1a (64-bit) checksum of every byte after the magic up to the checksum.  Version 1 files (no
+// checksum) still load.
+static uint64_t fnv1a64(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; i++) {
+    h ^= b[i];
+    h *= 0x100000001b3ULL;
+  }
+  return h;
+}
+static const uint64_t kFnvBasis = 0xcbf29ce484222325ULL;
+
 gp_status gp_model_save(const gp_model* M, const char* path) {
   if (!M || !path) return GP_ERR_INVALID;
   std::vector<float> buf((size_t)kPN * 3);
@@ -427,10 +441,16 @@ gp_status gp_model_save(const gp_model* M, const char* path) {
   }
   FILE* f = fopen(path, "wb");
   if (!f) return GP_ERR_INVALID;
-  const uint32_t ver = 1, np = (uint32_t)kPN;
+  const uint32_t ver = 2, np = (uint32_t)kPN;
   const int64_t step = M->step;
+  uint64_t h = kFnvBasis;
+  h = fnv1a64(h, &ver, 4);
+  h = fnv1a64(h, &np, 4);
+  h = fnv1a64(h, &step, 8);
+  h = fnv1a64(h, buf.data(), sizeof(float) * buf.size());
   bool ok = fwrite(kModelMagic, 1, 8, f) == 8 && fwrite(&ver, 4, 1, f) == 1 && fwrite(&np, 4, 1, f) == 1 &&
-            fwrite(&step, 8, 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+            fwrite(&step, 8, 1, f) == 1 && fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+            fwrite(&h, 8, 1, f) == 1;
   ok = (fclose(f) == 0) && ok;
   return ok ? GP_OK : GP_ERR_INVALID;
 }
@@ -443,10 +463,24 @@ gp_status gp_model_load(const char* path, gp_model** out) {
   char mg[8];
   uint32_t ver = 0, np = 0;
   int64_t step = 0;
+  uint64_t sum = 0;
   std::vector<float> buf((size_t)kPN * 3);
-  const bool ok = fread(mg, 1, 8, f) == 8 && memcmp(mg, kModelMagic, 8) == 0 && fread(&ver, 4, 1, f) == 1 &&
-                  ver == 1 && fread(&np, 4, 1, f) == 1 && np == (uint32_t)kPN && fread(&step, 8, 1, f) == 1 &&
-                  fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  bool ok = fread(mg, 1, 8, f) == 8 && memcmp(mg, kModelMagic, 8) == 0 && fread(&ver, 4, 1, f) == 1 &&
+            (ver == 1 || ver == 2) && fread(&np, 4, 1, f) == 1 && np == (uint32_t)kPN && fread(&step, 8, 1, f) == 1 &&
+            fread(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  if (ok && ver == 2) {
+    ok = fread(&sum, 8, 1, f) == 1;
+    uint64_t h = kFnvBasis;
+    h = fnv1a64(h, &ver, 4);
+    h = fnv1a64(h, &np, 4);
+    h = fnv1a64(h, &step, 8);
+    h = fnv1a64(h, buf.data(), sizeof(float) * buf.size());
+    ok = ok && h == sum;
+  }
+  if (ok) {  // nothing may follow
+    char extra;
+    ok = fread(&extra, 1, 1, f) == 0;
+  }
   fclose(f);
   if (!ok) return GP_ERR_INVALID;
   for (float x : buf)

@@ -130,6 +130,7 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
         ok[q] = k < d;
         us[q] = ok[q] ? g.adj[b + k] : 0;
         ws[q] = ok[q] ? g.W[b + k] : 0;
+        ok[q] = ok[q] && GP_IN(us[q], g.n, 1);
       }
 #pragma unroll
       for (int q = 0; q < 4; q++) {
@@ -186,7 +187,7 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     if (mate[v] != -1) continue;
     const int32_t u = pick[v];
-    if (u >= 0 && pick[u] == (int32_t)v) mate[v] = u;
+    if (u >= 0 && GP_IN(u, n, 2) && pick[u] == (int32_t)v) mate[v] = u;
   }
 }
 
@@ -222,7 +223,7 @@ __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* 
       }
 #pragma unroll
       for (int q = 0; q < 4; q++)
-        if (us[q] >= 0) {
+        if (us[q] >= 0 && GP_IN(us[q], g.n, 3)) {
           lk.offer(ws[q], (uint32_t)us[q], seed, (uint32_t)v);
           bytes += 12;
         }
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(1024)
     } else {
       for (int32_t q = threadIdx.x; q < d; q += blockDim.x) {
         const int32_t v = g.adj[b + q];
-        if (anchor[v] == h) ta[b + atomicAdd(&s_k, 1u)] = v;
+        if (GP_IN(v, g.n, 4) && anchor[v] == h) ta[b + atomicAdd(&s_k, 1u)] = v;
       }
     }
     __syncthreads();
@@ -582,6 +583,7 @@ __device__ void cmap_fill(const LevelGraph& g, const int32_t* __restrict__ mate,
                           int8_t* __restrict__ cfix = nullptr) {
   for (int64_t v = tid; v < g.n; v += stride) {
     const int32_t u = mate[v];
+    if (!GP_IN(u + 1, g.n + 1, 5)) continue;  // a partner id, or -1
     if (u < 0 || v < u) {
       const int32_t c = cmap[v];
       rep_of[c] = (int32_t)v;
@@ -735,6 +737,7 @@ void contract_level(const LevelGraph& g, const int32_t* mate, int32_t* cmap, Lev
   src.row_a = rep_of;
   src.row_b = mate_of;
   src.map = cmap;
+  src.map_n = g.n;
   src.drop_self = 1;
   merge_rows_unordered(src, nc, nc, cg.start, cg.deg, cg.adj, cg.W, F_CONTRACT_MERGE, cg.cap, s);
   dfree(rep_of, s);

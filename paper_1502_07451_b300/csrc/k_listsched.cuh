@@ -200,7 +200,7 @@ __device__ void ls_graph(const LsJob& J, int Pc, int Pg, LsOut* out) {
         int v = -1;
         long long arrive = 0;
         uint8_t pv = 0;
-        if (valid) {
+        if (valid && GP_IN(J.cols[e], n, 13)) {
           v = J.cols[e];
           pv = J.part[v];
           arrive = fu + (pv != pu ? (long long)J.w[e] : 0ll);
@@ -215,7 +215,7 @@ __device__ void ls_graph(const LsJob& J, int Pc, int Pg, LsOut* out) {
           amax = a > amax ? a : amax;
           cnt++;
         }
-        const bool leader = valid && lane == __ffs(grp) - 1;
+        const bool leader = v >= 0 && lane == __ffs(grp) - 1;
         bool released = false;
         long long rdy = 0;
         if (leader) {

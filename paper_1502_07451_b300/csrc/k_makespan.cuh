@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256)
     if (pu > 1 && sub == 0) atomicOr(bad_part, 1);
     const int64_t b = off[u], e_end = off[u + 1];
     for (int64_t e = b + sub; e < e_end; e += G)
-      if (part[cols[e]] != pu) s += (unsigned long long)w[e];
+      if (GP_IN(cols[e], n, 11) && part[cols[e]] != pu) s += (unsigned long long)w[e];
     if (sub == 0) bytes += 17ull + (unsigned long long)(e_end - b) * 9ull;
   }
   s = block_sum<unsigned long long>(s, sh);

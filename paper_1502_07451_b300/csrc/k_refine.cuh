@@ -147,7 +147,7 @@ __device__ void gain_all(const LevelGraph& g, const uint8_t* __restrict__ part, 
         }
 #pragma unroll
         for (int q = 0; q < 4; q++)
-          if (us[q] >= 0) acc += (part[us[q]] == p) ? -ws[q] : ws[q];
+          if (us[q] >= 0 && GP_IN(us[q], g.n, 6)) acc += (part[us[q]] == p) ? -ws[q] : ws[q];
       }
       if (sub == 0) bytes += 21ull + 13ull * (unsigned long long)d;
     }
@@ -247,7 +247,8 @@ __device__ void ref_cands(const LevelGraph& g, const uint8_t* __restrict__ part,
     long long acc = 0;
     for (int32_t q = lane; q < d; q += 32) {
       const long long w = g.W[b + q];
-      acc += (part[g.adj[b + q]] == p) ? -w : w;
+      const int32_t u = g.adj[b + q];
+      if (GP_IN(u, g.n, 7)) acc += (part[u] == p) ? -w : w;
     }
     acc = warp_sum64(acc);
     if (lane == 0) {
@@ -527,7 +528,7 @@ __device__ void ref_apply_body(const SelParams sp, Ctl* ctl, int r, const LevelG
       bool fresh = false;
       if (q < d) {
         u = g.adj[b + q];
-        fresh = atomicExch(&cand.stamp[u], tag) != tag;
+        fresh = GP_IN(u, g.n, 8) && atomicExch(&cand.stamp[u], tag) != tag;
       }
       const unsigned m = __ballot_sync(0xffffffffu, fresh);
       if (!m) continue;

@@ -51,6 +51,9 @@ __device__ __forceinline__ void row_entry(const TwoSrc& s, const RowView& v, int
     col = s.b_col[e];
     w = s.b_w64 ? s.b_w64[e] : (int64_t)s.b_w32[e];
   }
+#ifdef GP_CHECKED
+  if (s.map && s.map_n > 0 && !GP_IN(col, s.map_n, 12)) col = 0;  // recorded; an in-range id instead
+#endif
   if (s.map) col = s.map[col];
 }
 

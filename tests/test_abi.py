@@ -31,6 +31,18 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(gp.lib(), n)
 
 
+def test_checked_library_exports_the_same_symbols():
+    """libgp_checked.so (the same sources with in-kernel index tests) builds and exports every declared
+    entry point; the unchecked library reports -1 for the checked word without touching a GPU."""
+    from paper_1502_07451_b300 import build
+    path = build.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(gp_\w+)", out))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+    assert gp.gp_checked_site(False) == -1
+
+
 def test_bounds_match_oracle(oracle_mod):
     rng = np.random.default_rng(11)
     for _ in range(500):
@@ -61,3 +73,23 @@ def test_library_sources_do_not_reach_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 for needle in ("import oracle", "from oracle", "liboracle", "gp_oracle", "og_"):
                     assert needle not in text, (f, needle)
+
+
+def test_committed_checkpoint_format_and_checksum():
+    """The trained checkpoint is a version-2 file whose FNV-1a checksum (recomputed here, byte by byte)
+    matches, with 37,505 finite parameters and both Adam moments."""
+    import struct
+
+    import numpy as np
+
+    path = os.path.join(ROOT, "paper_1502_07451_b300", "models", "mpnn3_h64.bin")
+    d = open(path, "rb").read()
+    assert d[:8] == b"GPMPNN01"
+    ver, npar = struct.unpack_from("<II", d, 8)
+    assert ver == 2 and npar == 37505 and len(d) == 24 + 12 * npar + 8
+    h = 0xCBF29CE484222325
+    for b in d[8:-8]:
+        h = ((h ^ b) * 0x100000001B3) & ((1 << 64) - 1)
+    assert struct.unpack_from("<Q", d, len(d) - 8)[0] == h
+    vals = np.frombuffer(d, dtype="<f4", count=3 * npar, offset=24)
+    assert np.isfinite(vals).all() and (vals[2 * npar:] >= 0).all()
