@@ -195,6 +195,22 @@ def test_training_is_deterministic_and_checkpoints_roundtrip():
                         assert np.array_equal(gp.gp_model_get_params(M.h), gp.gp_model_get_params(M2))
                     finally:
                         gp.gp_model_destroy(M2)
+                    # the checksum: a flipped byte, a truncated or a longer file are refused
+                    raw = open(path, "rb").read()
+                    for bad in (raw[:100] + bytes([raw[100] ^ 1]) + raw[101:], raw[:-5], raw + b"\0"):
+                        with open(path, "wb") as f:
+                            f.write(bad)
+                        with pytest.raises(gp.GpError) as e:
+                            gp.gp_model_load(path)
+                        assert e.value.status == gp.GP_ERR_INVALID
+                    # a version-1 file (no checksum) still loads, with the same parameters
+                    with open(path, "wb") as f:
+                        f.write(raw[:8] + (1).to_bytes(4, "little") + raw[12:-8])
+                    M3 = gp.gp_model_load(path)
+                    try:
+                        assert np.array_equal(gp.gp_model_get_params(M3), finals[0])
+                    finally:
+                        gp.gp_model_destroy(M3)
         assert np.array_equal(finals[0], finals[1])  # same seed, same data: same parameters
     finally:
         for G in Gs:
