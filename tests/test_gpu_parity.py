@@ -439,46 +439,3 @@ def test_full_size_layered_1m_bit_exact():
     assert {k: res[k] for k in ores} == ores
     assert tr["n"] == otr["n"] and tr["a"] == otr["a"] and tr["rounds"] == otr["rounds"]
     assert ms == oracle.makespan(g, opart)
-
-
-def test_full_size_layered_16m():
-    """16M vertices, 128M edges (int64 offsets, 256M undirected entries): the plain and the learned
-    path.  The oracle's single-pass steps run on the GPU's splits at full size (cut, loads,
-    makespan); the learned path's proposal rule runs in the oracle from the GPU's logits.  With
-    GP_TEST_ORACLE_16M=1 the whole oracle partition runs too (minutes of host time)."""
-    g = gen.config_layered_16m()
-    n = g["n"]
-    cc = g["cpu_cost"].astype(np.int64)
-    cg = g["gpu_cost"].astype(np.int64)
-    with gp.Graph(dgraph(g)) as G:
-        part = torch.empty(n, dtype=torch.uint8, device="cuda")
-        res = G.partition(part)
-        p = host(part)
-        ms = G.makespan(part)
-        assert res["cut"] == oracle.cut(g, p)
-        assert res["load_cpu"] == int(cc[p == 0].sum()) and res["load_gpu"] == int(cg[p == 1].sum())
-        bc, bg = oracle.bounds(int(cc.sum()), int(cg.sum()))
-        assert (res["bound_cpu"], res["bound_gpu"]) == (bc, bg)
-        assert res["feasible"] == int(res["load_cpu"] <= bc and res["load_gpu"] <= bg)
-        assert ms == oracle.makespan(g, p)
-        if os.environ.get("GP_TEST_ORACLE_16M") == "1":
-            opart, ores = oracle.partition(g)
-            assert np.array_equal(p, opart) and {k: res[k] for k in ores} == ores
-        path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1502_07451_b300",
-                            "models", "mpnn3_h64.bin")
-        model = gp.gp_model_load(path)
-        try:
-            logits = torch.empty(n, dtype=torch.float32, device="cuda")
-            gp.gp_model_forward(model, G.h, logits)
-            rl = gp.gp_partition_learned(G.h, model, part)
-            pl = host(part)
-        finally:
-            gp.gp_model_destroy(model)
-        lg = logits.cpu().numpy()
-        assert np.isfinite(lg).all()
-        # the proposal rule on the GPU's logits, then the same refinement, in the oracle
-        if os.environ.get("GP_TEST_ORACLE_16M") == "1":
-            opl, orl = oracle.partition_learned(g, lg)
-            assert np.array_equal(pl, opl) and all(rl[k] == orl[k] for k in orl)
-        assert rl["cut"] == oracle.cut(g, pl)
-        assert rl["load_cpu"] == int(cc[pl == 0].sum()) and rl["load_gpu"] == int(cg[pl == 1].sum())
