@@ -117,10 +117,12 @@ class BatchGen:
             self.pool = None
 
 
-def profiled_traffic(family, workload="1m"):
-    """DRAM bytes per launch of `family` on `workload` ("1m" or "16m") from the committed ncu summary,
-    if one covers this family and workload and the kernel's sources are unchanged since the capture
-    (else None)."""
+def profiled_traffic(family, workload="1m", alg_bytes_per_launch=None):
+    """DRAM bytes per launch of `family` on `workload` ("1m" or "16m") from a committed ncu summary that
+    covers this family and workload and whose kernel sources are unchanged since the capture, else None.
+    Returns (bytes, source file, how): a summary gives either the family's bytes per launch
+    (traffic_bytes_per_launch, every launch of a step captured) or the DRAM / algorithmic ratio of one
+    captured launch (traffic_ratio), which scales this run's algorithmic bytes per launch."""
     import hashlib
     import glob
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -130,7 +132,7 @@ def profiled_traffic(family, workload="1m"):
                 if line.startswith("traffic_"):
                     k, _, v = line.partition(":")
                     kv[k.strip()] = v.strip()
-        if kv.get("traffic_kernel") != family or "traffic_bytes_per_launch" not in kv:
+        if kv.get("traffic_kernel") != family:
             continue
         if kv.get("traffic_workload", "1m") != workload:
             continue
@@ -138,8 +140,15 @@ def profiled_traffic(family, workload="1m"):
         for src in kv.get("traffic_sources", "").split():
             with open(os.path.join(ROOT, src), "rb") as f:
                 h.update(f.read())
-        if h.hexdigest() == kv.get("traffic_sources_sha256"):
-            return float(kv["traffic_bytes_per_launch"]), os.path.relpath(path, ROOT)
+        if h.hexdigest() != kv.get("traffic_sources_sha256"):
+            continue
+        rel = os.path.relpath(path, ROOT)
+        if "traffic_bytes_per_launch" in kv:
+            return float(kv["traffic_bytes_per_launch"]), rel, "DRAM bytes of every launch of one step / launches"
+        if "traffic_ratio" in kv and alg_bytes_per_launch:
+            return (float(kv["traffic_ratio"]) * alg_bytes_per_launch, rel,
+                    "DRAM / algorithmic bytes of the captured launch (%s) x this run's algorithmic bytes per launch"
+                    % kv["traffic_ratio"])
     return None
 
 
@@ -389,7 +398,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch object of the layered lines")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned objects of the layered lines")
     ap.add_argument("--profile-case", default=None,
-                    choices=["layered1m", "learned1m", "batch64", "layered4m", "layered16m"],
+                    choices=["layered1m", "learned1m", "batch64", "batch4096", "layered4m", "layered16m"],
                     help="run one small invocation for a profiler (no timing, no JSON line contract)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -654,10 +663,11 @@ def run_layered_line(args, rank, world, local_rank):
 
     res, ms = M["res"], M["makespan"]
     dom = M["roofline"]["kernel"]
-    traffic = profiled_traffic(dom, "16m" if big else "1m")
+    traffic = profiled_traffic(dom, "16m" if big else "1m", M["roofline"]["alg_bytes_per_launch"])
     roof = dict(M["roofline"])
     roof["traffic"] = traffic[0] if traffic else None
     roof["traffic_source"] = traffic[1] if traffic else None
+    roof["traffic_how"] = traffic[2] if traffic else None
     line = {
         "metric": METRIC, "value": M["value"], "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": M["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -688,8 +698,9 @@ def run_layered_line(args, rank, world, local_rank):
              "e2e": one_m["e2e"], "e2e_matches_device": one_m["e2e_ok"], "gpu_launches": one_m["launches"],
              "roofline": one_m["roofline"], "roofline_by_family": one_m["by_family"],
              "kernel_time_share": one_m["share"]}
-        t1 = profiled_traffic(one_m["roofline"]["kernel"], "1m")
-        o["roofline"] = dict(o["roofline"], traffic=t1[0] if t1 else None, traffic_source=t1[1] if t1 else None)
+        t1 = profiled_traffic(one_m["roofline"]["kernel"], "1m", one_m["roofline"]["alg_bytes_per_launch"])
+        o["roofline"] = dict(o["roofline"], traffic=t1[0] if t1 else None, traffic_source=t1[1] if t1 else None,
+                             traffic_how=t1[2] if t1 else None)
         if with_oracle:
             o["cpu_baseline"] = cpu1
         line["layered1m"] = o
@@ -1108,6 +1119,7 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True, golden_ok=True):
         "vertices": n_tot, "edges": m_tot,
         "value": K * count / (tot_ms / 1e3), "edges_per_sec": K * m_tot / (tot_ms / 1e3),
         "ms_per_step": tot_ms / K, "kernel_ms_per_step": kern_ms / K, "steps": K, "warmup": W,
+        "feasible": int(sum(r["feasible"] for r in res)), "cut_sum": int(sum(r["cut"] for r in res)),
         "step": "gp_batch_partition(4,096 resident handles, makespans on), one persistent launch",
         "schedule": gp.gp_batch_schedule_name(best),
         "autotune_ms": {gp.gp_batch_schedule_name(i): round(t, 2) for i, t in enumerate(sched_ms)},
@@ -1189,9 +1201,12 @@ def run_batch_line(args, rank, world, local_rank, bgen):
 
 def run_profile_case(name):
     """One invocation of the path, for a profiler: layered1m = one plain step (create, partition,
-    makespan) on the bench workload; layered4m / layered16m = the same on 4M / 16M-vertex layered DAGs
-    of width 16,000; learned1m = one learned step with the trained checkpoint; batch64 =
-    gp_batch_partition over 64 graphs of the batch recipe (sizes up to 10,000)."""
+    makespan) on the 1M DAG; layered4m / layered16m = the same on 4M / 16M-vertex layered DAGs of width
+    16,000; learned1m = one learned step with the trained checkpoint; batch64 = gp_batch_partition and
+    gp_batch_makespan_workers over 64 graphs of the batch recipe (sizes up to 10,000); batch4096 =
+    gp_graph_create_batch,
+    gp_batch_partition with makespans and gp_batch_makespan_workers over the whole 4,096-graph mix."""
+    bgen = BatchGen(held=False) if name == "batch4096" else None
     import torch
     import paper_1502_07451_b300 as gp
     from paper_1502_07451_b300 import gen
@@ -1217,15 +1232,29 @@ def run_profile_case(name):
         gp.gp_graph_destroy(h)
         torch.cuda.synchronize()
         print(json.dumps({"case": name, "cut": res["cut"], "makespan": mk}))
+    elif name == "batch4096":
+        graphs = bgen.graphs()
+        bgen.wait()
+        src = [dict({k: torch.from_numpy(np.ascontiguousarray(gg[k])).cuda() for k in keys}, n=gg["n"], m=gg["m"])
+               for gg in graphs]
+        hs, _ = gp.gp_graph_create_batch(src)
+        parts = [torch.zeros(max(gg["n"], 1), dtype=torch.uint8, device="cuda") for gg in graphs]
+        res, mks = gp.gp_batch_partition(hs, parts, makespans=True)
+        msw = gp.gp_batch_makespan_workers(hs, parts, 3, 1)
+        for h in hs:
+            gp.gp_graph_destroy(h)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res), "makespan_w31_sum": sum(msw)}))
     else:
         graphs = [gen.build_from_spec(it) for it in gen.batch_spec(64, nmin=100, nmax=10000, base_seed=0)]
         hs = [gp.gp_graph_create(gg["n"], gg["m"], *[torch.from_numpy(gg[k]).cuda() for k in keys]) for gg in graphs]
         parts = [torch.empty(gg["n"], dtype=torch.uint8, device="cuda") for gg in graphs]
         res, mks = gp.gp_batch_partition(hs, parts, makespans=True)
+        msw = gp.gp_batch_makespan_workers(hs, parts, 3, 1)
         for h in hs:
             gp.gp_graph_destroy(h)
         torch.cuda.synchronize()
-        print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res)}))
+        print(json.dumps({"case": name, "cut_sum": sum(r["cut"] for r in res), "makespan_w31_sum": sum(msw)}))
 
 
 def run_cholesky_line(args, rank, world, local_rank):
@@ -1339,6 +1368,7 @@ def run_cholesky_line(args, rank, world, local_rank):
                        "cut_plain_mean": float(np.mean([r["cut"] for r in pres])),
                        "makespan_learned": int(lmk[0]), "makespan_plain_mean": float(np.mean(pmk)),
                        "feasible_learned": int(sum(r["feasible"] for r in lres)),
+                       "feasible_plain": int(sum(r["feasible"] for r in pres)),
                        "create_s": create_s, "kernel_time_share": {f: round(prof[f]["total_ms"] / tot_ms, 4)
                                                                    for f in fams if prof[f]["launches"]}},
             "e2e": {"value": count / e2e_s, "unit": BATCH_UNIT, "h2d_bytes_per_step": h2d,
