@@ -117,9 +117,10 @@ class BatchGen:
             self.pool = None
 
 
-def profiled_traffic(family, workload="1m", alg_bytes_per_launch=None):
-    """DRAM bytes per launch of `family` on `workload` ("1m" or "16m") from a committed ncu summary that
-    covers this family and workload and whose kernel sources are unchanged since the capture, else None.
+def profiled_traffic(family, workload="1m", alg_bytes_per_launch=None, schedule=None):
+    """DRAM bytes per launch of `family` on `workload` ("1m", "16m" or "batch4096") from a committed ncu
+    summary that covers this family and workload (and, where the summary names one, this batch
+    schedule) and whose kernel sources are unchanged since the capture, else None.
     Returns (bytes, source file, how): a summary gives either the family's bytes per launch
     (traffic_bytes_per_launch, every launch of a step captured) or the DRAM / algorithmic ratio of one
     captured launch (traffic_ratio), which scales this run's algorithmic bytes per launch."""
@@ -135,6 +136,8 @@ def profiled_traffic(family, workload="1m", alg_bytes_per_launch=None):
         if kv.get("traffic_kernel") != family:
             continue
         if kv.get("traffic_workload", "1m") != workload:
+            continue
+        if kv.get("traffic_schedule", schedule) != schedule:
             continue
         h = hashlib.sha256()
         for src in kv.get("traffic_sources", "").split():
@@ -1138,6 +1141,10 @@ def bench_batch(graphs, K, W, stream, flush, with_cpu=True, golden_ok=True):
                      "peak": hbm_peak, "unit": "GB/s", "frac": alg / (bms * 1e-3) / 1e9 / hbm_peak,
                      "peak_kind": peak_kind, "traffic": None, "alg_bytes_per_launch": alg, "launch_ms": bms},
     }
+    if count == BATCH_COUNT:
+        tb = profiled_traffic("batch", "batch4096", alg, gp.gp_batch_schedule_name(best))
+        if tb:
+            out["roofline"].update(traffic=tb[0], traffic_source=tb[1], traffic_how=tb[2])
     if cpu:
         out["cpu_baseline"] = cpu
         if count == BATCH_COUNT and golden_ok:
@@ -1199,13 +1206,17 @@ def run_batch_line(args, rank, world, local_rank, bgen):
 
 
 
+PROFILE_BATCH_SCHEDULE = "cta512x2_sixteenth_rows"
+
+
 def run_profile_case(name):
     """One invocation of the path, for a profiler: layered1m = one plain step (create, partition,
     makespan) on the 1M DAG; layered4m / layered16m = the same on 4M / 16M-vertex layered DAGs of width
     16,000; learned1m = one learned step with the trained checkpoint; batch64 = gp_batch_partition and
     gp_batch_makespan_workers over 64 graphs of the batch recipe (sizes up to 10,000); batch4096 =
-    gp_graph_create_batch,
-    gp_batch_partition with makespans and gp_batch_makespan_workers over the whole 4,096-graph mix."""
+    gp_graph_create_batch, gp_batch_partition with makespans (schedule PROFILE_BATCH_SCHEDULE, the one
+    the bench's autotuning picks on this mix) and gp_batch_makespan_workers over the whole 4,096-graph
+    mix."""
     bgen = BatchGen(held=False) if name == "batch4096" else None
     import torch
     import paper_1502_07451_b300 as gp
@@ -1239,6 +1250,8 @@ def run_profile_case(name):
                for gg in graphs]
         hs, _ = gp.gp_graph_create_batch(src)
         parts = [torch.zeros(max(gg["n"], 1), dtype=torch.uint8, device="cuda") for gg in graphs]
+        names = [gp.gp_batch_schedule_name(i) for i in range(gp.gp_batch_schedule_count())]
+        gp.gp_batch_set_schedule(names.index(PROFILE_BATCH_SCHEDULE))
         res, mks = gp.gp_batch_partition(hs, parts, makespans=True)
         msw = gp.gp_batch_makespan_workers(hs, parts, 3, 1)
         for h in hs:

@@ -157,6 +157,40 @@ int num_sms() {
   return (d >= 0 && d < 64) ? g_sms[d] : 1;
 }
 
+int64_t l2_bytes() {
+  static int64_t v[64];
+  const int d = device_id();
+  if (d < 0 || d >= 64) return (int64_t)1 << 62;
+  if (v[d] == 0) {
+    int b = 0;
+    cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, d);
+    v[d] = b > 0 ? b : ((int64_t)1 << 62);
+  }
+  return v[d];
+}
+
+int resident_blocks(const void* kern, int threads, size_t smem) {
+  struct Key {
+    const void* k;
+    int t;
+    size_t m;
+    int d;
+  };
+  static std::vector<std::pair<Key, int>> cache;
+  static std::mutex mu;
+  const int d = device_id();
+  std::lock_guard<std::mutex> lk(mu);
+  for (auto& e : cache)
+    if (e.first.k == kern && e.first.t == threads && e.first.m == smem && e.first.d == d) return e.second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  cache.push_back({{kern, threads, smem, d}, occ});
+  return occ;
+}
+
 static void pool_setup() {
   const int d = device_id();
   std::lock_guard<std::mutex> lk(g_dev_mu);
@@ -593,15 +627,18 @@ static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, cons
     int32_t* in_src = g->in_src = g->own<int32_t>(m, s);
     int32_t* in_w = g->in_w = g->own<int32_t>(m, s);
     GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));
-    if (m) GP_LAUNCH(F_TRANSPOSE, k_indeg, grid_for(m, 256, 8), 256, 0, s, m, g->cols, indeg);
+    // grids of the scattering kernels: resident only, when their scatter targets exceed half the L2
+    if (m)
+      GP_LAUNCH(F_TRANSPOSE, k_indeg, grid_scatter((const void*)k_indeg, m, 256, 256, 4 * n, 8), 256, 0, s, m,
+                g->cols, indeg);
     scan_i32_to_i64(indeg, in_off, n, s);
     GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));  // reused as fill cursor
     if (n) {
       switch (makespan_group(n, m)) {  // lanes per row from the average out-degree
 #define GP_FI(GG)                                                                                           \
   case GG:                                                                                                  \
-    GP_LAUNCH(F_TRANSPOSE, k_fill_in<GG>, grid_for(n * GG, 256), 256, 0, s, n, g->off, g->cols, g->w, in_off, \
-              indeg, in_src, in_w, flags);                                                                  \
+    GP_LAUNCH(F_TRANSPOSE, k_fill_in<GG>, grid_scatter((const void*)k_fill_in<GG>, n * GG, 256, 256, 8 * m + 4 * n), \
+              256, 0, s, n, g->off, g->cols, g->w, in_off, indeg, in_src, in_w, flags);                     \
     break;
         GP_FI(2) GP_FI(4) GP_FI(8) GP_FI(16) GP_FI(32)
 #undef GP_FI
@@ -715,8 +752,8 @@ static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, cons
         switch (makespan_group(n, m)) {  // lanes per position from the average in-degree
 #define GP_LF(GG)                                                                                          \
   case GG:                                                                                                 \
-    GP_LAUNCH(F_TRANSPOSE, k_lo_fill<GG>, grid_for(n * GG, 256), 256, 0, sl, n, g->lev_vtx, in_off, in_src,  \
-              in_w, pos_of, g->lo_off, g->lo_src, g->lo_w);                                                \
+    GP_LAUNCH(F_TRANSPOSE, k_lo_fill<GG>, grid_scatter((const void*)k_lo_fill<GG>, n * GG, 256, 256, 4 * n), 256, \
+              0, sl, n, g->lev_vtx, in_off, in_src, in_w, pos_of, g->lo_off, g->lo_src, g->lo_w);          \
     break;
           GP_LF(2) GP_LF(4) GP_LF(8) GP_LF(16) GP_LF(32)
 #undef GP_LF

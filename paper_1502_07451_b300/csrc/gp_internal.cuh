@@ -98,6 +98,23 @@ T* dnew(int64_t count, cudaStream_t s) {
 int num_sms();
 int device_id();
 
+// Blocks of a grid-stride kernel whose scattered accesses (atomics and stores at data-dependent
+// positions) cover `scatter_bytes`: when those are larger than half of the L2, at most as many blocks
+// as fit on the device at once, so that the grid's passes cover the index range once, in order, and
+// the positions a stretch of it scatters to stay in L2 while it is written (a larger grid runs in
+// waves, each sweeping the whole range again after the previous wave's lines were evicted); else
+// grid_for's bound (more blocks than fit: later blocks balance the load).  resident_blocks: blocks
+// per SM of `kern` at `threads` threads (occupancy query, cached); l2_bytes: the device's L2 size.
+int resident_blocks(const void* kern, int threads, size_t smem);
+int64_t l2_bytes();
+inline unsigned grid_scatter(const void* kern, int64_t work, int per_block, int threads, int64_t scatter_bytes,
+                             int max_per_sm = 16) {
+  const int64_t want = (work + per_block - 1) / per_block;
+  const int64_t per_sm = scatter_bytes > l2_bytes() / 2 ? resident_blocks(kern, threads, 0) : max_per_sm;
+  const int64_t cap = (int64_t)num_sms() * per_sm;
+  return (unsigned)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
 // ------------------------------------------------------------------------------------------------
 // Device helpers.
 // ------------------------------------------------------------------------------------------------

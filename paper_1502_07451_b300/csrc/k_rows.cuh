@@ -57,6 +57,34 @@ __device__ __forceinline__ void row_entry(const TwoSrc& s, const RowView& v, int
   if (s.map) col = s.map[col];
 }
 
+// Row entries read once and merged rows written once by the hash tiers go through the cache with an
+// evict-first policy (ld.global.cs / st.global.cs), so that on graphs larger than the L2 they do not
+// push out the coarse-id map, which every row gathers from.
+template <typename T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+  return __ldcs(p);
+}
+template <typename T>
+__device__ __forceinline__ void st_stream(T* p, T v) {
+  __stcs(p, v);
+}
+__device__ __forceinline__ void row_entry_stream(const TwoSrc& s, const RowView& v, int64_t i, int32_t& col,
+                                                 int64_t& w) {
+  if (i < v.a_len) {
+    const int64_t e = v.a_beg + i;
+    col = ld_stream(s.a_col + e);
+    w = s.a_w64 ? ld_stream(s.a_w64 + e) : (int64_t)ld_stream(s.a_w32 + e);
+  } else {
+    const int64_t e = v.b_beg + (i - v.a_len);
+    col = ld_stream(s.b_col + e);
+    w = s.b_w64 ? ld_stream(s.b_w64 + e) : (int64_t)ld_stream(s.b_w32 + e);
+  }
+#ifdef GP_CHECKED
+  if (s.map && s.map_n > 0 && !GP_IN(col, s.map_n, 12)) col = 0;
+#endif
+  if (s.map) col = s.map[col];
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
   unsigned m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
@@ -464,7 +492,7 @@ __global__ void __launch_bounds__(WARPS * 32)
       if (i >= len) continue;
       int32_t col;
       int64_t w;
-      row_entry(s, v, i, col, w);
+      row_entry_stream(s, v, i, col, w);
       bytes += entry_bytes(s, i < v.a_len);
       if (s.drop_self && col == (int32_t)r) continue;
       unsigned sl = ((uint32_t)col * 0x9E3779B1u) >> shift;
@@ -490,8 +518,8 @@ __global__ void __launch_bounds__(WARPS * 32)
       const unsigned m = __ballot_sync(0xffffffffu, c);
       if (c) {
         const int pos = out + __popc(m & lt);
-        adj_out[ob + pos] = K[slot[p]];
-        W_out[ob + pos] = (int64_t)V[slot[p]];
+        st_stream(adj_out + ob + pos, K[slot[p]]);
+        st_stream(W_out + ob + pos, (int64_t)V[slot[p]]);
         K[slot[p]] = kEmptyKey;
         V[slot[p]] = 0ull;
       }
@@ -625,7 +653,7 @@ __global__ void __launch_bounds__(THREADS)
       if (i >= len) continue;
       int32_t col;
       int64_t w;
-      row_entry(s, v, i, col, w);
+      row_entry_stream(s, v, i, col, w);
       bytes += entry_bytes(s, i < v.a_len);
       if (s.drop_self && col == (int32_t)r) continue;
       unsigned sl = ((uint32_t)col * 0x9E3779B1u) >> shift;
@@ -652,8 +680,8 @@ __global__ void __launch_bounds__(THREADS)
       wpos = __shfl_sync(0xffffffffu, wpos, 0);
       if (c) {
         const unsigned pos = wpos + __popc(m & lt);
-        adj_out[ob + pos] = K[slot[p]];
-        W_out[ob + pos] = (int64_t)V[slot[p]];
+        st_stream(adj_out + ob + pos, K[slot[p]]);
+        st_stream(W_out + ob + pos, (int64_t)V[slot[p]]);
         K[slot[p]] = kEmptyKey;
         V[slot[p]] = 0ull;
       }
