@@ -633,12 +633,14 @@ static gp_status graph_create(int64_t n, int64_t m, const int64_t* offsets, cons
                 g->cols, indeg);
     scan_i32_to_i64(indeg, in_off, n, s);
     GP_CUDA(cudaMemsetAsync(indeg, 0, sizeof(int32_t) * (n > 0 ? n : 1), s));  // reused as fill cursor
+    unsigned long long* fill_next = A.get<unsigned long long>(1);
+    GP_CUDA(cudaMemsetAsync(fill_next, 0, sizeof(unsigned long long), s));
     if (n) {
       switch (makespan_group(n, m)) {  // lanes per row from the average out-degree
 #define GP_FI(GG)                                                                                           \
   case GG:                                                                                                  \
     GP_LAUNCH(F_TRANSPOSE, k_fill_in<GG>, grid_scatter((const void*)k_fill_in<GG>, n * GG, 256, 256, 8 * m + 4 * n), \
-              256, 0, s, n, g->off, g->cols, g->w, in_off, indeg, in_src, in_w, flags);                     \
+              256, 0, s, n, g->off, g->cols, g->w, in_off, indeg, in_src, in_w, flags, fill_next);          \
     break;
         GP_FI(2) GP_FI(4) GP_FI(8) GP_FI(16) GP_FI(32)
 #undef GP_FI

@@ -53,23 +53,35 @@ __global__ void k_indeg(int64_t m, const int32_t* __restrict__ cols, int32_t* __
     atomicAdd(&indeg[cols[e]], 1);
 }
 
-// in-CSR fill (warp per source row); also detects self-loops
+// in-CSR fill (G lanes per source row); also detects self-loops.  Blocks take chunks of consecutive
+// source rows in order from a counter (`next`, zero at launch), so the whole grid works on neighbouring
+// rows at any time: on a DAG whose edges stay near their source in id order, the in-rows the rows
+// scatter to stay in L2 while their sectors fill up (a static grid-stride split lets the blocks drift
+// apart, and the window of in-rows being written grows beyond the L2).
 template <int G>  // lanes per row
 __global__ void __launch_bounds__(256)
     k_fill_in(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
               const int32_t* __restrict__ w, const int64_t* __restrict__ in_off, int32_t* cursor,
-              int32_t* __restrict__ in_src, int32_t* __restrict__ in_w, int* flags) {
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int sub = threadIdx.x % G;
-  const int64_t gw = tid / G, nw = ((int64_t)gridDim.x * blockDim.x) / G;
-  for (int64_t u = gw; u < n; u += nw) {
-    const int64_t b = off[u], e_end = off[u + 1];
-    for (int64_t e = b + sub; e < e_end; e += G) {
-      const int32_t v = cols[e];
-      if (v == (int32_t)u) atomicOr(flags, VF_SELFLOOP);
-      const int64_t pos = in_off[v] + atomicAdd(&cursor[v], 1);
-      in_src[pos] = (int32_t)u;
-      in_w[pos] = w[e];
+              int32_t* __restrict__ in_src, int32_t* __restrict__ in_w, int* flags, unsigned long long* next) {
+  constexpr int kGroups = 256 / G, kRows = 4 * kGroups;  // rows per chunk: four per group
+  __shared__ long long s_base;
+  const int sub = threadIdx.x % G, group = threadIdx.x / G;
+  for (;;) {
+    if (threadIdx.x == 0) s_base = (long long)atomicAdd(next, (unsigned long long)kRows);
+    __syncthreads();
+    const int64_t base = s_base;
+    __syncthreads();  // every thread has read the chunk before thread 0 takes the next
+    if (base >= n) break;
+    const int64_t end = base + kRows < n ? base + kRows : n;
+    for (int64_t u = base + group; u < end; u += kGroups) {
+      const int64_t b = off[u], e_end = off[u + 1];
+      for (int64_t e = b + sub; e < e_end; e += G) {
+        const int32_t v = cols[e];
+        if (v == (int32_t)u) atomicOr(flags, VF_SELFLOOP);
+        const int64_t pos = in_off[v] + atomicAdd(&cursor[v], 1);
+        in_src[pos] = (int32_t)u;
+        in_w[pos] = w[e];
+      }
     }
   }
 }
