@@ -100,18 +100,22 @@ struct LazyKey {
 // calling thread and the number of threads sharing the level (grid or one CTA).  Returns, per
 // thread, whether it recorded a pick.  FIX: g.fix is set (a separate instance: the check costs the
 // plain picks 10 registers).
-template <int G, bool FIX = false>
+template <int G, bool FIX = false, bool LIST = false>
 __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed, long long mC, long long mG,
                            const int32_t* __restrict__ mate, int32_t* __restrict__ pick,
-                           uint8_t* __restrict__ alive, int64_t tid, int64_t stride, bool all_free = false) {
+                           uint8_t* __restrict__ alive, int64_t tid, int64_t stride, bool all_free = false,
+                           const int32_t* __restrict__ list = nullptr, int64_t count = 0) {
   __shared__ unsigned long long sacc[32];
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
   const unsigned gmask = group_mask(G);
   unsigned long long bytes = 0;
   bool picked = false;
-  for (int64_t v = group; v < g.n; v += ngroups) {
-    if (sub == 0) bytes += 5;
+  // every vertex, or (LIST) the vertices of `list`: those still unmatched and alive after the previous round
+  const int64_t nv = LIST ? count : g.n;
+  for (int64_t i = group; i < nv; i += ngroups) {
+    const int64_t v = LIST ? (int64_t)list[i] : i;
+    if (sub == 0) bytes += LIST ? 9 : 5;
     if (mate[v] != -1 || !alive[v]) continue;  // same v across the group: uniform
     const int64_t b = g.start[v];
     const int32_t d = g.deg[v];
@@ -174,20 +178,53 @@ __device__ bool match_pick(const LevelGraph& g, int64_t capC, int64_t capG, uint
   account(F_MATCH_PICK, bytes, sacc);
   return picked;
 }
-template <int G, bool FIX>
-__global__ void __launch_bounds__(256)
+template <int G, bool FIX, bool LIST>
+__global__ void __launch_bounds__(256, 5)  // 5 blocks per SM: at most 51 registers
     k_match_pick(LevelGraph g, int64_t capC, int64_t capG, uint64_t seed, const long long* __restrict__ maxw,
                  const int32_t* __restrict__ mate, int32_t* __restrict__ pick, uint8_t* __restrict__ alive,
-                 int all_free) {
-  match_pick<G, FIX>(g, capC, capG, seed, maxw[0], maxw[1], mate, pick, alive,
-                (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x, all_free != 0);
+                 int all_free, const int32_t* __restrict__ list, const unsigned* list_cnt) {
+  match_pick<G, FIX, LIST>(g, capC, capG, seed, maxw[0], maxw[1], mate, pick, alive,
+                           (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x,
+                           all_free != 0, list, LIST ? (int64_t)*list_cnt : 0);
 }
 
-__global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    if (mate[v] != -1) continue;
-    const int32_t u = pick[v];
-    if (u >= 0 && GP_IN(u, n, 2) && pick[u] == (int32_t)v) mate[v] = u;
+// Handshakes of a round: v and u are matched when each picked the other.  Over every vertex, or over
+// `list_in`; with `list_out`, the vertices that stay unmatched and alive (they can still be matched)
+// are appended there for the next round, whose picks then run on whole groups of such vertices
+// instead of skipping the matched ones (the list's order does not matter: a pick depends only on the
+// state at the start of its round).
+__global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick,
+                                const uint8_t* __restrict__ alive, const int32_t* __restrict__ list_in,
+                                const unsigned* cnt_in, int32_t* __restrict__ list_out, unsigned* cnt_out) {
+  const int64_t nv = list_in ? (int64_t)*cnt_in : n;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  // whole warps step together, so that a warp appends its survivors with one atomic
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t wb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; wb < nv; wb += stride) {
+    const int64_t i = wb + lane;
+    bool keep = false;
+    int32_t v = -1;
+    if (i < nv) {
+      v = list_in ? list_in[i] : (int32_t)i;
+      if (mate[v] == -1) {
+        const int32_t u = pick[v];
+        if (u >= 0 && GP_IN(u, n, 2) && pick[u] == v)
+          mate[v] = u;
+        else
+          keep = alive[v] != 0;
+      }
+    }
+    if (list_out) {
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (m) {
+        const int first = __ffs(m) - 1;
+        unsigned base = 0;
+        if (lane == first) base = atomicAdd(cnt_out, (unsigned)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, first);
+        if (keep) list_out[base + __popc(m & lt)] = v;
+      }
+    }
   }
 }
 
@@ -638,22 +675,44 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
   GP_CUDA(cudaMemsetAsync(maxw, 0, 2 * sizeof(long long), s));
   GP_LAUNCH(F_MISC, k_match_init, grid_for(n, 256), 256, 0, s, n, g.vC, g.vG, capC, capG, mate, pick, alive);
   GP_LAUNCH(F_MISC, k_max_weights, grid_for(n, 256, 4), 256, 0, s, n, g.vC, g.vG, maxw);
+  // round 0 picks over every vertex; each later round over the list of the vertices the previous
+  // round's handshakes left unmatched and alive (two lists, used in turn; a counter per round)
+  int32_t* lists[2] = {dnew<int32_t>(n, s), dnew<int32_t>(n, s)};
+  unsigned* cnts = dnew<unsigned>(rounds > 0 ? rounds : 1, s);
+  GP_CUDA(cudaMemsetAsync(cnts, 0, sizeof(unsigned) * (size_t)(rounds > 0 ? rounds : 1), s));
   for (int r = 0; r < rounds; r++) {
+    const int32_t* lin = r == 0 ? nullptr : lists[(r - 1) & 1];
+    const unsigned* cin = r == 0 ? nullptr : cnts + (r - 1);
+    int32_t* lout = r + 1 < rounds ? lists[r & 1] : nullptr;
+    unsigned* cout = r + 1 < rounds ? cnts + r : nullptr;
     switch (G) {
-#define GP_MP(GG)                                                                                       \
-  case GG:                                                                                             \
-    if (g.fix)                                                                                         \
-      GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, true>), grid_for(n * GG, 256), 256, 0, s, g, capC, capG, \
-                seed, (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0);                        \
-    else                                                                                               \
-      GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, false>), grid_for(n * GG, 256), 256, 0, s, g, capC,      \
-                capG, seed, (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0);                  \
+#define GP_MP1(GG, FX, LS)                                                                               \
+  GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, FX, LS>), grid_for(n * GG, 256), 256, 0, s, g, capC, capG, seed, \
+            (const long long*)maxw, mate, pick, alive, r == 0 ? 1 : 0, lin, cin)
+#define GP_MP(GG)                                 \
+  case GG:                                        \
+    if (g.fix) {                                  \
+      if (lin)                                    \
+        GP_MP1(GG, true, true);                   \
+      else                                        \
+        GP_MP1(GG, true, false);                  \
+    } else {                                      \
+      if (lin)                                    \
+        GP_MP1(GG, false, true);                  \
+      else                                        \
+        GP_MP1(GG, false, false);                 \
+    }                                             \
     break;
       GP_MP(2) GP_MP(4) GP_MP(8) GP_MP(16) GP_MP(32)
 #undef GP_MP
+#undef GP_MP1
     }
-    GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick);
+    GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick,
+              (const uint8_t*)alive, lin, cin, lout, cout);
   }
+  dfree(lists[0], s);
+  dfree(lists[1], s);
+  dfree(cnts, s);
   if (twohop) {
     // every unmatched vertex into the bucket of its anchor (count, scan, scatter), then a warp per
     // anchor pairs its bucket; buckets of more than kSatCap vertices, a block each
