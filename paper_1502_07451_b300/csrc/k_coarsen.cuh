@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256, 5)  // 5 blocks per SM: at most 51 regist
 // state at the start of its round).
 __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick,
                                 const uint8_t* __restrict__ alive, const int32_t* __restrict__ list_in,
-                                const unsigned* cnt_in, int32_t* __restrict__ list_out, unsigned* cnt_out) {
+                                const unsigned* cnt_in, int32_t* __restrict__ list_out, unsigned* cnt_out,
+                                int keep_dead) {
   const int64_t nv = list_in ? (int64_t)*cnt_in : n;
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -212,7 +213,7 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
         if (u >= 0 && GP_IN(u, n, 2) && pick[u] == v)
           mate[v] = u;
         else
-          keep = alive[v] != 0;
+          keep = keep_dead || alive[v] != 0;
       }
     }
     if (list_out) {
@@ -229,17 +230,21 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
 }
 
 // anchor of every unmatched vertex: its best neighbour under the matching key (no filters)
-template <int G>
+template <int G, bool LIST = false>
 __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* __restrict__ mate,
                              int32_t* __restrict__ anchor, uint8_t* __restrict__ is_anchor, int64_t tid,
-                             int64_t stride, int32_t* __restrict__ scnt = nullptr) {
+                             int64_t stride, int32_t* __restrict__ scnt = nullptr,
+                             const int32_t* __restrict__ list = nullptr, int64_t count = 0) {
   __shared__ unsigned long long sacc[32];
   const int64_t group = tid / G, ngroups = stride / G;
   const int sub = threadIdx.x % G;
   const unsigned gmask = group_mask(G);
   unsigned long long bytes = 0;
-  for (int64_t v = group; v < g.n; v += ngroups) {
-    if (mate[v] != -1) {
+  // every vertex, or (LIST) the vertices of `list`: the unmatched ones, whose anchors are still -1
+  const int64_t nv = LIST ? count : g.n;
+  for (int64_t i = group; i < nv; i += ngroups) {
+    const int64_t v = LIST ? (int64_t)list[i] : i;
+    if (!LIST && mate[v] != -1) {
       if (sub == 0) {
         anchor[v] = -1;
         bytes += 8;
@@ -280,12 +285,13 @@ __device__ void match_anchor(const LevelGraph& g, uint64_t seed, const int32_t* 
   }
   account(F_TWOHOP, bytes, sacc);
 }
-template <int G>
+template <int G, bool LIST>
 __global__ void __launch_bounds__(256)
     k_anchor(LevelGraph g, uint64_t seed, const int32_t* __restrict__ mate, int32_t* __restrict__ anchor,
-             uint8_t* __restrict__ is_anchor, int32_t* __restrict__ scnt) {
-  match_anchor<G>(g, seed, mate, anchor, is_anchor, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                  (int64_t)gridDim.x * blockDim.x, scnt);
+             uint8_t* __restrict__ is_anchor, int32_t* __restrict__ scnt, const int32_t* __restrict__ list,
+             const unsigned* list_cnt) {
+  match_anchor<G, LIST>(g, seed, mate, anchor, is_anchor, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                        (int64_t)gridDim.x * blockDim.x, scnt, list, LIST ? (int64_t)*list_cnt : 0);
 }
 
 // every anchored vertex into its anchor's bucket: sat[soff[a] .. soff[a + 1]) (in no particular order;
@@ -683,8 +689,10 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
   for (int r = 0; r < rounds; r++) {
     const int32_t* lin = r == 0 ? nullptr : lists[(r - 1) & 1];
     const unsigned* cin = r == 0 ? nullptr : cnts + (r - 1);
-    int32_t* lout = r + 1 < rounds ? lists[r & 1] : nullptr;
-    unsigned* cout = r + 1 < rounds ? cnts + r : nullptr;
+    // the last round lists every vertex it leaves unmatched, alive or not, for the two-hop anchors
+    const bool last_for_anchors = twohop && r + 1 == rounds;
+    int32_t* lout = (r + 1 < rounds || last_for_anchors) ? lists[r & 1] : nullptr;
+    unsigned* cout = (r + 1 < rounds || last_for_anchors) ? cnts + r : nullptr;
     switch (G) {
 #define GP_MP1(GG, FX, LS)                                                                               \
   GP_LAUNCH(F_MATCH_PICK, (k_match_pick<GG, FX, LS>), grid_for(n * GG, 256), 256, 0, s, g, capC, capG, seed, \
@@ -707,12 +715,14 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
 #undef GP_MP
 #undef GP_MP1
     }
+    // (the last round's confirm then runs over every vertex: those that died in earlier rounds are
+    // unmatched too, and the two-hop pairing anchors them as well)
     GP_LAUNCH(F_MATCH_CONFIRM, k_match_confirm, grid_for(n, 256), 256, 0, s, n, mate, pick,
-              (const uint8_t*)alive, lin, cin, lout, cout);
+              (const uint8_t*)alive, last_for_anchors ? nullptr : lin, last_for_anchors ? nullptr : cin, lout, cout,
+              last_for_anchors ? 1 : 0);
   }
-  dfree(lists[0], s);
-  dfree(lists[1], s);
-  dfree(cnts, s);
+  const int32_t* alist = (twohop && rounds > 0) ? lists[(rounds - 1) & 1] : nullptr;
+  const unsigned* acnt = (twohop && rounds > 0) ? cnts + (rounds - 1) : nullptr;
   if (twohop) {
     // every unmatched vertex into the bucket of its anchor (count, scan, scatter), then a warp per
     // anchor pairs its bucket; buckets of more than kSatCap vertices, a block each
@@ -726,11 +736,16 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
     int32_t* tb = dnew<int32_t>(n, s);
     GP_CUDA(cudaMemsetAsync(scnt, 0, sizeof(int32_t) * (size_t)n, s));
     GP_CUDA(cudaMemsetAsync(big_cnt, 0, sizeof(unsigned), s));
+    if (alist) GP_CUDA(cudaMemsetAsync(anchor, 0xff, sizeof(int32_t) * (size_t)n, s));  // -1: no anchor
     switch (G) {
 #define GP_AN(GG)                                                                                         \
   case GG:                                                                                               \
-    GP_LAUNCH(F_TWOHOP, k_anchor<GG>, grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor,             \
-              (uint8_t*)nullptr, scnt);                                                                  \
+    if (alist)                                                                                           \
+      GP_LAUNCH(F_TWOHOP, (k_anchor<GG, true>), grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor,   \
+                (uint8_t*)nullptr, scnt, alist, acnt);                                                   \
+    else                                                                                                 \
+      GP_LAUNCH(F_TWOHOP, (k_anchor<GG, false>), grid_for(n * GG, 256), 256, 0, s, g, seed, mate, anchor,  \
+                (uint8_t*)nullptr, scnt, (const int32_t*)nullptr, (const unsigned*)nullptr);             \
     break;
       GP_AN(2) GP_AN(4) GP_AN(8) GP_AN(16) GP_AN(32)
 #undef GP_AN
@@ -753,6 +768,9 @@ void match_level(const LevelGraph& g, int64_t capC, int64_t capG, uint64_t seed,
     dfree(ta, s);
     dfree(tb, s);
   }
+  dfree(lists[0], s);
+  dfree(lists[1], s);
+  dfree(cnts, s);
   GP_CHECK_LAUNCH();
   dfree(pick, s);
   dfree(alive, s);
