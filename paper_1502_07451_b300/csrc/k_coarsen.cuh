@@ -189,21 +189,22 @@ __global__ void __launch_bounds__(256, 5)  // 5 blocks per SM: at most 51 regist
 }
 
 // Handshakes of a round: v and u are matched when each picked the other.  Over every vertex, or over
-// `list_in`; with `list_out`, the vertices that stay unmatched and alive (they can still be matched)
-// are appended there for the next round, whose picks then run on whole groups of such vertices
-// instead of skipping the matched ones (the list's order does not matter: a pick depends only on the
-// state at the start of its round).
-__global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick,
-                                const uint8_t* __restrict__ alive, const int32_t* __restrict__ list_in,
-                                const unsigned* cnt_in, int32_t* __restrict__ list_out, unsigned* cnt_out,
-                                int keep_dead) {
+// `list_in` (launched with 256 threads); with `list_out`, the vertices that stay unmatched and alive
+// (with keep_dead: every unmatched vertex, for the two-hop anchors) are appended there for the next
+// round, whose picks then run on whole groups of such vertices instead of skipping the matched ones
+// (the list's order does not matter: a pick depends only on the state at the start of its round).
+__global__ void __launch_bounds__(256)
+    k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int32_t* __restrict__ pick,
+                    const uint8_t* __restrict__ alive, const int32_t* __restrict__ list_in, const unsigned* cnt_in,
+                    int32_t* __restrict__ list_out, unsigned* cnt_out, int keep_dead) {
   const int64_t nv = list_in ? (int64_t)*cnt_in : n;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  // whole warps step together, so that a warp appends its survivors with one atomic
+  // whole blocks (of 8 warps) step together, so that a block appends its survivors with one atomic
+  __shared__ unsigned s_wc[8], s_base;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t wb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; wb < nv; wb += stride) {
-    const int64_t i = wb + lane;
+  for (int64_t bb = (int64_t)blockIdx.x * blockDim.x; bb < nv; bb += stride) {
+    const int64_t i = bb + threadIdx.x;
     bool keep = false;
     int32_t v = -1;
     if (i < nv) {
@@ -218,13 +219,18 @@ __global__ void k_match_confirm(int64_t n, int32_t* __restrict__ mate, const int
     }
     if (list_out) {
       const unsigned m = __ballot_sync(0xffffffffu, keep);
-      if (m) {
-        const int first = __ffs(m) - 1;
-        unsigned base = 0;
-        if (lane == first) base = atomicAdd(cnt_out, (unsigned)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, first);
-        if (keep) list_out[base + __popc(m & lt)] = v;
+      if (lane == 0) s_wc[wid] = __popc(m);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int q = 0; q < 8; q++) tot += s_wc[q];
+        s_base = tot ? atomicAdd(cnt_out, tot) : 0;
       }
+      unsigned before = 0;
+      for (int q = 0; q < wid; q++) before += s_wc[q];
+      __syncthreads();
+      if (keep) list_out[s_base + before + __popc(m & lt)] = v;
+      __syncthreads();  // s_wc and s_base are rewritten by the next step
     }
   }
 }
