@@ -187,7 +187,9 @@ def test_step_match_and_contract(lv):
     name, n, off, adj, W, vC, vG, BC, BG = lv
     d = [dev(off), dev(adj), dev(W), dev(vC), dev(vG)]
     for seed in (0, 17):
-        for rounds, twohop in ((1, 0), (4, 0), (4, 1)):
+        # (two-hop pairing anchors the vertices the last round's confirm lists; with 0 rounds the anchor
+        # pass runs over every vertex, with 1 the first round's confirm writes that list)
+        for rounds, twohop in ((1, 0), (4, 0), (4, 1), (0, 1), (1, 1), (2, 1)):
             mate = torch.empty(n, dtype=torch.int32, device="cuda")
             gp.gp_step_match(n, *d, BC // 8, BG // 8, seed, rounds, twohop, mate)
             want = oracle.match(n, off, adj, W, vC, vG, BC // 8, BG // 8, seed, rounds)
